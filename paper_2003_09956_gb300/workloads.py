@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs for the pseudo-projection solver.
+
+This module only draws problem data (matrices, right-hand sides, starting
+points, translation directions).  It holds none of the method's arithmetic,
+imports nothing from the CUDA binding and nothing from the oracle, so the
+tests can feed byte-identical inputs to both.
+
+Workload families (the paper's own test system of Section 5 is a figure that
+did not survive; these stand in for it):
+
+* ``model_system(n)``: the scalable cube-with-a-cut-corner system
+  0 <= x_j <= 200, sum_j x_j <= 200 (n - 1) + 100  (m = 2n + 1 rows), started
+  outside the cut corner at x0 ~ U[300, 400]^n.
+* ``dense_system(m, n)``: a_ij ~ N(0, 1), an interior point z ~ U(-1, 1)^n,
+  b0 = A z + U(0.1, 1.0), a unit translation direction v = g / ||g||,
+  Av = A v (both in FP64) and x0 ~ N(0, 25 I) rounded to binary32.
+  ``grid="bf16"`` or ``grid="e4m3"`` first rounds A onto the bfloat16 grid, or
+  onto a per-row power-of-two-scaled FP8 E4M3 grid, with torch's own
+  conversions, so that the system is exactly representable in that storage
+  format; b0 and Av are then computed from the rounded A.
+* ``small_polytope(n, m)``: a small random system around a known interior
+  point, for brute-force checks.
+
+Large matrices are drawn in fixed row chunks, each from its own
+``SeedSequence`` child, so the bytes do not depend on the thread count.
+"""
+from __future__ import annotations
+
+import concurrent.futures as _cf
+import os
+
+import numpy as np
+
+_CHUNK_ROWS = 2048
+
+
+def _chunk_rngs(seed: int, m: int):
+    nchunks = (m + _CHUNK_ROWS - 1) // _CHUNK_ROWS
+    children = np.random.SeedSequence(seed).spawn(nchunks + 1)
+    return children[:nchunks], np.random.Generator(np.random.PCG64(children[-1]))
+
+
+def _threads() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def gaussian_matrix(m: int, n: int, seed: int) -> np.ndarray:
+    """m x n float32 matrix with N(0, 1) entries, drawn in row chunks."""
+    A = np.empty((m, n), np.float32)
+    seqs, _ = _chunk_rngs(seed, m)
+
+    def fill(c):
+        r0 = c * _CHUNK_ROWS
+        r1 = min(m, r0 + _CHUNK_ROWS)
+        g = np.random.Generator(np.random.PCG64(seqs[c]))
+        g.standard_normal((r1 - r0, n), dtype=np.float32, out=A[r0:r1])
+
+    with _cf.ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(fill, range(len(seqs))))
+    return A
+
+
+def round_to_grid(A: np.ndarray, grid: str | None) -> np.ndarray:
+    """Round A (float32) onto a storage grid with torch's conversions."""
+    if grid is None or grid == "f32":
+        return A
+    import torch
+
+    if grid == "bf16":
+        out = np.empty_like(A)
+        for r0 in range(0, A.shape[0], 8192):
+            t = torch.from_numpy(A[r0:r0 + 8192])
+            out[r0:r0 + 8192] = t.to(torch.bfloat16).to(torch.float32).numpy()
+        return out
+    if grid == "e4m3":
+        out = np.empty_like(A)
+        for r0 in range(0, A.shape[0], 8192):
+            blk = A[r0:r0 + 8192]
+            amax = np.abs(blk).max(axis=1).astype(np.float64)
+            f, e2 = np.frexp(amax)
+            # smallest power of two 2^e with amax / 2^e <= 448 = 0.875 * 2^9
+            e = np.where(f <= 0.875, e2 - 9, e2 - 8)
+            e = np.where(amax > 0, e, 0)
+            s = np.ldexp(1.0, e).astype(np.float32)[:, None]
+            t = torch.from_numpy(np.ascontiguousarray(blk / s))
+            q = t.to(torch.float8_e4m3fn).to(torch.float32).numpy()
+            out[r0:r0 + 8192] = q * s
+        return out
+    raise ValueError("unknown grid %r" % (grid,))
+
+
+def _matvec_f64(A: np.ndarray, v: np.ndarray) -> np.ndarray:
+    out = np.empty(A.shape[0], np.float64)
+    step = 4096
+
+    def part(r0):
+        out[r0:r0 + step] = A[r0:r0 + step].astype(np.float64) @ v
+
+    with _cf.ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(part, range(0, A.shape[0], step)))
+    return out
+
+
+def dense_system(m: int, n: int, seed: int, grid: str | None = None,
+                 x0_std: float = 5.0) -> dict:
+    """The non-stationary dense random system (see the module docstring)."""
+    A = round_to_grid(gaussian_matrix(m, n, seed), grid)
+    _, g = _chunk_rngs(seed, m)
+    z = g.uniform(-1.0, 1.0, n)
+    slack = g.uniform(0.1, 1.0, m)
+    dirn = g.standard_normal(n)
+    v = dirn / np.sqrt(np.sum(dirn * dirn))
+    x0 = g.normal(0.0, x0_std, n).astype(np.float32).astype(np.float64)
+    b0 = _matvec_f64(A, z) + slack
+    Av = _matvec_f64(A, v)
+    return {"A": A, "b0": b0, "Av": Av, "x0": x0, "z": z, "v": v,
+            "m": m, "n": n, "seed": seed, "grid": grid}
+
+
+def model_system(n: int, seed: int) -> dict:
+    """0 <= x_j <= 200 and sum x_j <= 200(n-1)+100, x0 ~ U[300, 400]^n."""
+    m = 2 * n + 1
+    A = np.zeros((m, n), np.float64)
+    b0 = np.zeros(m, np.float64)
+    idx = np.arange(n)
+    A[idx, idx] = -1.0           # -x_j <= 0
+    A[n + idx, idx] = 1.0        #  x_j <= 200
+    b0[n:2 * n] = 200.0
+    A[2 * n, :] = 1.0            #  sum_j x_j <= 200(n-1) + 100
+    b0[2 * n] = 200.0 * (n - 1) + 100.0
+    g = np.random.Generator(np.random.PCG64(seed))
+    x0 = g.uniform(300.0, 400.0, n)
+    z = np.full(n, 100.0)        # strictly interior point
+    return {"A": A, "b0": b0, "Av": None, "x0": x0, "z": z, "m": m, "n": n,
+            "seed": seed}
+
+
+def small_polytope(n: int, m: int, seed: int, spread: float = 3.0) -> dict:
+    """Small random bounded system around an interior point z.
+
+    Rows: the 2n box faces |x_j - z_j| <= 2 plus m - 2n random rows
+    a ~ N(0, 1) with b = a.z + U(0.1, 1).  z is strictly interior."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    z = g.uniform(-1.0, 1.0, n)
+    rows, rhs = [], []
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        rows.append(e.copy())
+        rhs.append(z[j] + 2.0)
+        rows.append(-e)
+        rhs.append(-z[j] + 2.0)
+    for _ in range(max(0, m - 2 * n)):
+        a = g.standard_normal(n)
+        rows.append(a)
+        rhs.append(float(a @ z) + g.uniform(0.1, 1.0))
+    A = np.array(rows, np.float64)
+    b0 = np.array(rhs, np.float64)
+    x0 = z + g.normal(0.0, spread, n) * 3.0
+    return {"A": A, "b0": b0, "Av": None, "x0": x0, "z": z, "m": A.shape[0],
+            "n": n, "seed": seed}
