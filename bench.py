@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Throughput of the pseudo-projection iteration (AP / ModAP) on GB300.
+
+One step = one iteration of the method over the whole system: the tick of
+b(k) = b0 + k rho Av, the fused Map over all m rows (residuals, positive
+slices, per-CTA sums), the deterministic Reduce, the stopping test and the
+step x <- x - lambda y / h.  Default workload: the dense random system
+m = 131072, n = 16384 (a_ij ~ N(0, 1), rho = 1e-4 per tick), A stored in
+binary32 (8 GiB, far larger than L2, so no flush is needed between steps);
+the bfloat16 and FP8-E4M3 storage of the same system are measured in the
+same run and reported under "variants".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nsli|reference]
+
+Multi-GPU (torchrun): every rank solves its own independent system
+(replicas, weak scaling); `value` = iterations of all ranks / max time.
+`--impl reference` times the FP64 CPU oracle on the host cores on a row
+sample of the same workload (the baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "dense-131072x16384": {"m": 131072, "n": 16384, "rho": 1e-4, "seed": 2005},
+    "dense-32768x8192": {"m": 32768, "n": 8192, "rho": 1e-4, "seed": 2004},
+}
+ELEM_BYTES = {"f32": 4, "bf16": 2, "fp8": 1, "f64": 8}
+METRIC = "ModAP iterations/sec"
+UNIT = "iterations/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="nsli", choices=["nsli", "reference"])
+    ap.add_argument("--workload", default="dense-131072x16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--variants", default="bf16,fp8",
+                    help="other storage types measured in the same run ('' for none)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def map_bytes(m, n, storage):
+    """Algorithmic bytes of one Map launch: A once, the 12-byte (16 with the
+    FP8 row scale) per-row record b0, Av, 1/||a||^2, and x."""
+    per_row = 16 if storage == "fp8" else 12
+    return m * n * ELEM_BYTES[storage] + m * per_row + 4 * n
+
+
+def step_bytes(m, n, storage):
+    """Algorithmic bytes of one iteration: the Map's, plus x written back."""
+    return map_bytes(m, n, storage) + 4 * n
+
+
+def kernels_sha():
+    src = os.path.join(ROOT, "paper_2003_09956_gb300", "csrc", "nsli_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+
+
+def profiled_traffic(workload, storage):
+    """DRAM bytes per Map launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "map_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernels_sha()
+    for line in open(path):
+        f = line.split()
+        if len(f) < 4 or line.startswith("#"):
+            continue
+        kv = dict(x.split("=", 1) for x in f if "=" in x)
+        if kv.get("workload") == workload and kv.get("storage") == storage and kv.get("kernels_sha") == sha:
+            return float(kv["traffic_bytes_per_launch"])
+    return None
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.out = os.path.join("/tmp", "nsli_clocks_%d.csv" % os.getpid())
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(p, m_full, seconds, rho):
+    """The FP64 oracle as it stands, single thread, on the first rows of the
+    workload; rate scaled by rows (its cost per iteration is linear in m)."""
+    import oracle
+
+    rows = min(2048, p["A"].shape[0])
+    A = np.ascontiguousarray(p["A"][:rows], dtype=np.float64)
+    b0 = p["b0"][:rows]
+    Av = p["Av"][:rows]
+    n2, _ = oracle.norms2(A)
+    x = p["x0"].copy()
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        _, x, _, _, _ = oracle.iteration(A, b0, Av, rho, k, n2, x)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or k >= 1000:
+            break
+    rate = k / el * rows / m_full
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of the FP64 C oracle (1 thread) over the first %d of %d rows "
+                      "(n=%d) in %.1f s; rate scaled by %d/%d rows" % (k, rows, m_full, A.shape[1], el,
+                                                                      rows, m_full)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    from paper_2003_09956_gb300 import workloads
+
+    p = workloads.dense_system(w["m"], w["n"], seed=w["seed"], rows=(0, 2048))
+    per_step_s = min(20.0, max(0.5, 90.0 / max(1, args.steps)))
+    # warm-up steps, then K timed steps, each a bounded sample
+    for _ in range(min(args.warmup, 3)):
+        cpu_baseline(p, w["m"], 0.5, w["rho"])
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(p, w["m"], per_step_s, w["rho"]))
+    el = time.perf_counter() - t0
+    rate = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload + " f32-generated, FP64 oracle on a row sample",
+                       "m": w["m"], "n": w["n"], "rho": w["rho"]},
+            "cpu_baseline": dict(vals[-1], value=rate),
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": el}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_storage(nsli, torch, p, storage, w, steps, warmup, dist, world):
+    """Create the solver for one storage type, warm up, time `steps`
+    iterations (graph replays), then one kernel-by-kernel pass."""
+    stream = torch.cuda.Stream()
+    s = nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage, stream=stream.cuda_stream)
+    s.iterate(warmup, rho=w["rho"])
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = s.launch_count()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        s.iterate(steps, rho=w["rho"], block_iters=min(steps, 50))
+        e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    launches = s.launch_count() - l0
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kpass = min(steps, 100)
+    map_ms, red_ms = s.iterate_timed(kpass, rho=w["rho"])
+    mv, mn = s.residual_max()
+    return s, stream, {"ms": ms, "launches": launches, "map_ms_avg": map_ms / kpass,
+                       "reduce_ms_avg": red_ms / kpass, "kernel_pass_ms_per_step": (map_ms + red_ms) / kpass,
+                       "max_viol_f64": mv, "max_viol_norm_f64": mn}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_2003_09956_gb300 import nsli, workloads
+
+    nsli.load()
+    w = WORKLOADS[args.workload]
+    m, n = w["m"], w["n"]
+    t_gen = time.perf_counter()
+    p = workloads.dense_system(m, n, seed=w["seed"] + rank)
+    t_gen = time.perf_counter() - t_gen
+    K, W = args.steps, max(3, args.warmup)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    s, stream, main_run = time_storage(nsli, torch, p, args.storage, w, K, W, dist, world)
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: each step copies
+    # that tick's right-hand side in from pinned memory, iterates once and
+    # reads x back
+    Ke = min(K, 50)
+    snaps = [np.ascontiguousarray(p["b0"] + (W + K + 100 + k) * w["rho"] * p["Av"]) for k in range(Ke)]
+    b_pin = torch.empty((Ke, m), dtype=torch.float64, pin_memory=True).numpy()
+    for k in range(Ke):
+        b_pin[k] = snaps[k]
+    x_pin = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    s.sync()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(Ke):
+        s.update_b(b_pin[k], tick=0)
+        s.iterate(1, rho=0.0)
+        s.get_x(out=x_pin)
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    s.close()
+
+    peak, peak_kind = measured_peak()
+    value = world * K / (main_run["ms"] / 1000.0)
+    mb = map_bytes(m, n, args.storage)
+    achieved = mb / (main_run["map_ms_avg"] / 1000.0) / 1e9
+    traffic = profiled_traffic(args.workload, args.storage)
+
+    variants = {}
+    for st in [v for v in args.variants.split(",") if v and v != args.storage]:
+        sv, _, r = time_storage(nsli, torch, p, st, w, K, W, dist, world)
+        sv.close()
+        vb = map_bytes(m, n, st)
+        v_val = world * K / (r["ms"] / 1000.0)
+        variants[st] = {"value": v_val, "unit": UNIT, "ms_per_step": r["ms"] / K,
+                        "vs_f32": v_val / value,
+                        "map_gbs": vb / (r["map_ms_avg"] / 1000.0) / 1e9,
+                        "map_frac_of_measured_hbm": vb / (r["map_ms_avg"] / 1000.0) / 1e9 / peak,
+                        "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, m, args.cpu_seconds, w["rho"])
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": main_run["ms"] / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": "%s %s storage, rho=%g per tick, RELAXED lambda=1" % (args.workload, args.storage,
+                                                                                   w["rho"]),
+                   "m": m, "n": n, "storage": args.storage, "rho": w["rho"],
+                   "l2": "inputs larger than L2 (A is %.1f GiB), no flush" % (m * n * ELEM_BYTES[args.storage] / 2**30),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "graph_block_iters": min(K, 50)},
+        "roofline": {"bound": "hbm", "kernel": "map_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": mb,
+                     "map_ms_avg": main_run["map_ms_avg"], "reduce_ms_avg": main_run["reduce_ms_avg"],
+                     "kernel_pass_ms_per_step": main_run["kernel_pass_ms_per_step"],
+                     "step_gbs": step_bytes(m, n, args.storage) * value / world / 1e9},
+        "e2e": {"value": world * Ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": m * 8,
+                "d2h_bytes_per_step": n * 8},
+        "gpu_launches": main_run["launches"],
+        "clocks": clk,
+        "max_viol_f64": main_run["max_viol_f64"],
+        "variants": variants,
+        "generate_s": t_gen,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

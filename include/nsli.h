@@ -1,0 +1,202 @@
+/*
+ * nsli.h -- C ABI of the GB300 pseudo-projection solver for (non-stationary)
+ * systems of linear inequalities A x <= b(t).
+ *
+ * Method: Sokolinsky & Sokolinskaya, "Scalable Parallel Algorithm for Solving
+ * Non-stationary Systems of Linear Inequalities" (2020).
+ *   Section 2, Eq. 7   positive slice  rho+_i(x) = max(<a_i,x> - b_i, 0) / ||a_i||^2 * a_i
+ *   Section 2, Eq. 8   phi(x) = y / h, y = sum_i rho+_i(x), h = #non-zero slices
+ *   Section 2, Eq. 10  eps-membership: for all i, r_i <= 0 or |r_i| / ||a_i|| < eps
+ *   Section 2, Eq. 12  ModAP step psi(x) = lambda * phi / ||phi|| = lambda * y / ||y||
+ *   Section 3, Eq. 13  the Map F_x(a_i, b_i) = rho+_i(x), then Reduce(+)
+ *   Section 5          non-stationarity as a translation of the polytope
+ *
+ * One iteration (the "hot path"):
+ *   b_i(k) = b0_i + k * rho * (A v)_i                      (tick; fused into the Map)
+ *   r_i = <a_i, x> - b_i(k);  y = sum_{r_i > 0} r_i / ||a_i||^2 * a_i;  h = #{r_i > 0}
+ *   stopping test on (x_k, b(k)); then
+ *   RELAXED: x <- x - lambda * y / h        (Algorithm 1, Eq. 8 with relaxation lambda)
+ *   MODAP:   x <- x - lambda * y / ||y||    (Eq. 12)
+ *   k <- k + 1
+ *
+ * Conventions for every call:
+ *   - Every function returns an int status (NSLI_OK = 0, > 0 informational,
+ *     < 0 error) and never aborts the process.
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the handle's device; the library detects
+ *     which.  Arrays are dense, contiguous, in the element type stated.
+ *   - All device work of a handle is issued on the stream given to
+ *     nsli_create; calls that return host results synchronise that stream.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef NSLI_H
+#define NSLI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsli_solver *nsli_handle;
+
+/* element types: storage of A on the device, and source type of A */
+enum {
+    NSLI_F64 = 0,      /* IEEE binary64; the Map accumulates in binary64   */
+    NSLI_F32 = 1,      /* IEEE binary32; the Map accumulates in binary32   */
+    NSLI_BF16 = 2,     /* bfloat16 (round-to-nearest-even from binary32)   */
+    NSLI_FP8E4M3 = 3   /* FP8 E4M3 codes with a power-of-two scale per row */
+};
+
+/* step rules */
+enum {
+    NSLI_RULE_RELAXED = 0, /* x <- x - lambda * y / h      (Eq. 8)  */
+    NSLI_RULE_MODAP = 1    /* x <- x - lambda * y / ||y||  (Eq. 12) */
+};
+
+/* stopping rules, evaluated on the Map at (x_k, b(k)) at the top of each
+ * iteration (STEP after the update) */
+enum {
+    NSLI_STOP_NONE = 0,        /* no test: run a fixed number of iterations  */
+    NSLI_STOP_STEP = 1,        /* ||x_{k+1} - x_k|| < eps, or h == 0          */
+    NSLI_STOP_EPSMEM = 2,      /* Eq. 10: max_i r_i / ||a_i|| < eps           */
+    NSLI_STOP_MAXVIOL_REL = 3  /* max_i r_i <= eps * max_i |b_i(k)|           */
+};
+
+/* status and return codes */
+enum {
+    NSLI_OK = 0,
+    NSLI_NOT_CONVERGED = 1,    /* max_iter reached without the stop rule     */
+    NSLI_ERR_ARG = -1,         /* invalid argument                           */
+    NSLI_ERR_ZERO_ROW = -2,    /* a row of A is zero (the method needs a_i != 0) */
+    NSLI_ERR_NONFINITE = -3,   /* NaN or Inf in A, b, Av, x or norms         */
+    NSLI_ERR_OOM = -4,         /* device allocation failed                   */
+    NSLI_ERR_CUDA = -5,        /* a CUDA runtime call failed (see nsli_last_error) */
+    NSLI_ERR_TIMEOUT = -6,     /* a bounded device wait expired              */
+    NSLI_ERR_UNSUPPORTED = -7  /* valid but outside this build's limits      */
+};
+
+typedef struct {
+    double lambda;       /* step length / relaxation, > 0                          */
+    int32_t rule;        /* NSLI_RULE_*                                             */
+    int32_t stop;        /* NSLI_STOP_*                                             */
+    double eps;          /* threshold of the stopping rule, >= 0                   */
+    int64_t max_iter;    /* nsli_solve: maximum number of x-updates, >= 0           */
+    int32_t block_iters; /* iterations per captured CUDA graph; 0 selects 32        */
+    int32_t reserved;    /* must be 0                                               */
+    double rho;          /* translation per tick: b(k) = b0 + k * rho * Av          */
+} nsli_params;
+
+typedef struct {
+    int64_t iters;            /* x-updates performed by this call               */
+    int64_t tick;             /* tick k after the call                          */
+    int32_t status;           /* NSLI_OK, NSLI_NOT_CONVERGED or an error code   */
+    int32_t reserved;
+    int64_t h;                /* violated rows at the final point (binary64 check) */
+    double max_viol;          /* max_i (a_i.x - b_i(k)), binary64, stored A      */
+    double max_viol_norm;     /* max_i (a_i.x - b_i(k)) / ||a_i||, binary64      */
+    double max_abs_b;         /* max_i |b_i(k)|                                  */
+    double last_step_norm;    /* ||x_k - x_{k-1}|| of the last update, binary64 */
+} nsli_result;
+
+/* Create a solver for the m x n system A x <= b0 + k rho Av.
+ *   storage   NSLI_F64 / NSLI_F32 / NSLI_BF16 / NSLI_FP8E4M3: how A is held on
+ *             the device.  BF16 rounds each binary32 entry to nearest even;
+ *             FP8E4M3 stores e4m3(a_ij / s_i) with s_i the smallest power of
+ *             two such that max_j |a_ij| / s_i <= 448 (saturating, nearest
+ *             even).  The solved system is the stored one.
+ *   a_dtype   NSLI_F64 or NSLI_F32: element type of the source A.  BF16 and
+ *             FP8E4M3 storage need an NSLI_F32 source.
+ *   A         host or device, row-major, m rows of lda elements (lda >= n);
+ *             copied, not retained.
+ *   b0        host or device, m doubles: right-hand side at tick 0.
+ *   norms2    host or device, m doubles ||a_i||^2, or NULL to compute them
+ *             in binary64 on the device from the stored entries.
+ *   Av        host or device, m doubles (A v for the translation direction
+ *             v), or NULL for a stationary right-hand side.
+ *   x0        host or device, n doubles: the starting point (rounded to the
+ *             accumulation type: binary32 unless storage is NSLI_F64).
+ *   stream    a cudaStream_t on the current device (not the legacy default
+ *             stream: iteration blocks are captured into CUDA graphs), or
+ *             NULL to let the handle create and own a non-blocking stream.
+ * Errors: NSLI_ERR_ARG (m, n < 1, lda < n, bad enum, NULL required pointer),
+ * NSLI_ERR_ZERO_ROW, NSLI_ERR_NONFINITE, NSLI_ERR_OOM, NSLI_ERR_CUDA,
+ * NSLI_ERR_UNSUPPORTED (n beyond the register-resident row limit: 16384 for
+ * binary32 / bf16 / fp8 storage, 8192 for binary64).  On error *out is NULL
+ * and nothing is leaked.  The handle owns all its device memory until
+ * nsli_destroy. */
+int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage,
+                int32_t a_dtype, const void *A, int64_t lda, const double *b0,
+                const double *norms2, const double *Av, const double *x0,
+                void *stream);
+
+/* Replace b0 (host or device, m doubles; NULL keeps the current b0) and set
+ * the tick k used by the next iteration (tick < 0 keeps the current tick).
+ * Section 5: the data update step of each iteration. */
+int nsli_update_b(nsli_handle h, const double *b0, int64_t tick);
+
+/* Run exactly n_iter iterations (Map, Reduce, step, tick) with no stopping
+ * test (p->stop is ignored); an iteration with h == 0 makes no step.  Issues
+ * the work asynchronously on the handle's stream and returns without
+ * synchronising.  n_iter >= 0. */
+int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter);
+
+/* The same n_iter iterations as nsli_iterate, launched kernel by kernel
+ * with a CUDA event pair around every kernel on the handle's stream.
+ * kernel_ms[0] receives the summed device time of the Map kernels and
+ * kernel_ms[1] that of the Reduce-and-step kernels, in milliseconds.
+ * Synchronises.  For attributing time to kernels (roofline figures). */
+int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter,
+                       double *kernel_ms);
+
+/* Iterate until the stopping rule holds or p->max_iter x-updates were made.
+ * Tests taken in binary32 are confirmed in binary64 on the stored A (the
+ * binary64 check decides; a rejected candidate costs one more iteration).
+ * Synchronises.  out receives the final binary64 check.  Returns out->status. */
+int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out);
+
+/* Binary64 feasibility check of the current x against the stored A and
+ * b(k) at the current tick (Eq. 10): max_i r_i and max_i r_i / ||a_i||.
+ * Either output pointer may be NULL.  Synchronises. */
+int nsli_residual_max(nsli_handle h, double *max_viol, double *max_viol_norm);
+
+/* One Map + Reduce (Eq. 13, Reduce(+)) at the current x and tick, without a
+ * step: y (host or device, n doubles), the violated-row count, and
+ * stats[0..2] = max r_i, max r_i / ||a_i||, max |b_i| in the accumulation
+ * type.  Any output may be NULL.  Synchronises. */
+int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats);
+
+/* Copy the current x out (host or device, n doubles) / set it. Synchronise. */
+int nsli_get_x(nsli_handle h, double *x);
+int nsli_set_x(nsli_handle h, const double *x);
+
+/* Diagnostics: the exact values of stored rows row0 .. row0+rows-1 as
+ * doubles (FP8 storage: code * row scale), written row-major with n values
+ * per row to `out` (host or device, rows * n doubles), and the binary64
+ * ||a_i||^2 the solver uses (host or device, m doubles).  Synchronise. */
+int nsli_get_stored_rows(nsli_handle h, int64_t row0, int64_t rows, double *out);
+int nsli_get_norms2(nsli_handle h, double *out);
+
+/* Progress of the last nsli_iterate / nsli_solve (device state).  The
+ * binary64 fields of out are those of the last check made, or 0.  Synchronises. */
+int nsli_get_result(nsli_handle h, nsli_result *out);
+
+/* Number of kernels the handle has launched so far (graph nodes included). */
+int64_t nsli_launch_count(nsli_handle h);
+
+/* Wait for all work of the handle. */
+int nsli_sync(nsli_handle h);
+
+/* Release every resource of the handle (NULL is allowed). */
+void nsli_destroy(nsli_handle h);
+
+/* Static description of a status code. */
+const char *nsli_strerror(int code);
+
+/* Text of the last error recorded on the handle ("" if none). */
+const char *nsli_last_error(nsli_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSLI_H */

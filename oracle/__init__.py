@@ -84,6 +84,10 @@ def _load():
         lib.oracle_solve.argtypes = [i64, i64, P, P, P, dbl, i64, P, P, dbl, ip,
                                      ip, dbl, i64, P, P]
         lib.oracle_solve.restype = None
+        lib.oracle_map_reduce_f32.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_map_reduce_f32.restype = None
+        lib.oracle_norms2_f32.argtypes = [i64, i64, P, P]
+        lib.oracle_norms2_f32.restype = i64
         lib.oracle_quantize_bf16.argtypes = [i64, P, P]
         lib.oracle_quantize_bf16.restype = None
         lib.oracle_quantize_e4m3_rows.argtypes = [i64, i64, P, P, P]
@@ -101,7 +105,14 @@ def _ptr(a: np.ndarray | None):
 
 
 def norms2(A) -> tuple[np.ndarray, int]:
-    """||a_i||^2 per row in FP64 and the number of zero rows (Section 2)."""
+    """||a_i||^2 per row in FP64 and the number of zero rows (Section 2).
+    A float32 matrix is read as binary32 and widened entry by entry."""
+    if isinstance(A, np.ndarray) and A.dtype == np.float32:
+        A = np.ascontiguousarray(A)
+        m, n = A.shape
+        n2 = np.empty(m, np.float64)
+        zero = _load().oracle_norms2_f32(m, n, _ptr(A), _ptr(n2))
+        return n2, int(zero)
     A = _f64(A)
     m, n = A.shape
     n2 = np.empty(m, np.float64)
@@ -119,14 +130,21 @@ def tick_b(b0, Av, rho: float, k: int) -> np.ndarray:
 
 
 def map_reduce(A, b, n2, x) -> dict:
-    """Map (Eq. 13 / Eq. 7) then Reduce(+) at x with right-hand side b."""
-    A, b, n2, x = _f64(A), _f64(b), _f64(n2), _f64(x)
+    """Map (Eq. 13 / Eq. 7) then Reduce(+) at x with right-hand side b.
+    A float32 matrix is read as binary32 and widened entry by entry."""
+    if isinstance(A, np.ndarray) and A.dtype == np.float32:
+        A = np.ascontiguousarray(A)
+        fn = _load().oracle_map_reduce_f32
+    else:
+        A = _f64(A)
+        fn = _load().oracle_map_reduce
+    b, n2, x = _f64(b), _f64(n2), _f64(x)
     m, n = A.shape
     y = np.empty(n, np.float64)
     r = np.empty(m, np.float64)
     h = ctypes.c_int64()
     mv, mn, mb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _load().oracle_map_reduce(m, n, _ptr(A), _ptr(b), _ptr(n2), _ptr(x), _ptr(y),
+    fn(m, n, _ptr(A), _ptr(b), _ptr(n2), _ptr(x), _ptr(y),
                               ctypes.byref(h), ctypes.byref(mv), ctypes.byref(mn),
                               ctypes.byref(mb), _ptr(r))
     return {"y": y, "h": int(h.value), "maxviol": mv.value, "maxnorm": mn.value,

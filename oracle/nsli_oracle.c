@@ -138,6 +138,64 @@ void oracle_map_reduce(int64_t m, int64_t n, const double *A, const double *b,
     *maxb = mb;
 }
 
+/* The same Map and Reduce for a matrix held as binary32 values: each entry is
+ * widened to double before use, so the arithmetic is that of
+ * oracle_map_reduce on the exact values (used for large systems, where a
+ * double copy of A would not fit beside the binary32 one). */
+void oracle_map_reduce_f32(int64_t m, int64_t n, const float *A,
+                           const double *b, const double *n2, const double *x,
+                           double *y, int64_t *h, double *maxviol,
+                           double *maxnorm, double *maxb, double *r)
+{
+    for (int64_t j = 0; j < n; ++j)
+        y[j] = 0.0;
+    int64_t count = 0;
+    double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        const float *a = A + i * n;
+        double dot = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            dot = dot + (double)a[j] * x[j];
+        double ri = dot - b[i];
+        if (r != NULL)
+            r[i] = ri;
+        if (ri > mv)
+            mv = ri;
+        double rn = ri / sqrt(n2[i]);
+        if (rn > mn)
+            mn = rn;
+        if (fabs(b[i]) > mb)
+            mb = fabs(b[i]);
+        if (ri > 0.0) {
+            double c = ri / n2[i];
+            for (int64_t j = 0; j < n; ++j)
+                y[j] = y[j] + c * (double)a[j];
+            count = count + 1;
+        }
+    }
+    *h = count;
+    *maxviol = mv;
+    *maxnorm = mn;
+    *maxb = mb;
+}
+
+/* ||a_i||^2 of binary32 rows, accumulated in double. */
+int64_t oracle_norms2_f32(int64_t m, int64_t n, const float *A, double *n2)
+{
+    int64_t zero_rows = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double a = (double)A[i * n + j];
+            s = s + a * a;
+        }
+        n2[i] = s;
+        if (s == 0.0)
+            zero_rows = zero_rows + 1;
+    }
+    return zero_rows;
+}
+
 static int stop_test_passes(int stop, double eps, double maxviol,
                             double maxnorm, double maxb)
 {

@@ -1,0 +1,797 @@
+// nsli_api.cu -- host side of the C ABI declared in include/nsli.h.
+//
+// Owns the device buffers of one problem, picks the launch shape of the Map
+// kernel from n and the storage type, captures blocks of iterations into
+// CUDA graphs, and runs the solve loop (graph block, read 64-byte state,
+// binary64 confirmation of candidate stops).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "nsli.h"
+#include "nsli_internal.h"
+
+using namespace nsli;
+
+struct nsli_solver {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int storage = NSLI_F32;
+    long long m = 0, n = 0, ld = 0;
+    int elem_bytes = 4, epv = 4, row_bytes = 0, nv = 0;
+    int vpt = 1, consumers = 32, R = 1, nstage = 2, stage_stride = 0;
+    size_t smem = 0;
+    int G = 1, red_grid = 1, num_sms = 1;
+    long long rows_base = 0;
+    int rows_rem = 0;
+
+    void *A = nullptr, *meta = nullptr, *x = nullptr, *part_y = nullptr;
+    double *b0_64 = nullptr, *av_64 = nullptr, *n2_64 = nullptr, *part_dx = nullptr, *ybuf = nullptr,
+           *dtmp = nullptr;
+    float *scale = nullptr;
+    PartStat *part_stat = nullptr;
+    DevState *st = nullptr;
+    VerOut *ver = nullptr;
+    int *flags = nullptr;
+
+    DevState *st_host = nullptr;  // pinned
+    VerOut *ver_host = nullptr;   // pinned
+    int *flags_host = nullptr;    // pinned
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    long long launches = 0;
+
+    nsli_result last_check{};
+    std::string last_error;
+};
+
+namespace {
+
+int set_err(nsli_solver *h, int code, const std::string &msg)
+{
+    if (h)
+        h->last_error = msg;
+    return code;
+}
+
+int cuda_err(nsli_solver *h, cudaError_t e, const char *what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation)
+        return set_err(h, NSLI_ERR_OOM, msg);
+    return set_err(h, NSLI_ERR_CUDA, msg);
+}
+
+#define CK(call, what)                                                                                       \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return cuda_err(h, e_, what);                                                                    \
+    } while (0)
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_all(nsli_solver *h)
+{
+    if (!h)
+        return;
+    if (h->graph)
+        cudaGraphExecDestroy(h->graph);
+    void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
+                   h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags};
+    for (void *p : dev)
+        if (p)
+            cudaFree(p);
+    if (h->st_host)
+        cudaFreeHost(h->st_host);
+    if (h->ver_host)
+        cudaFreeHost(h->ver_host);
+    if (h->flags_host)
+        cudaFreeHost(h->flags_host);
+    if (h->own_stream && h->stream)
+        cudaStreamDestroy(h->stream);
+}
+
+// Launch shape of the Map kernel (see nsli_kernels.cu): rows are padded to
+// whole 16-byte vectors; each consumer thread owns vpt vectors of every row.
+int choose_config(nsli_solver *h)
+{
+    switch (h->storage) {
+    case NSLI_F64: h->elem_bytes = 8; h->epv = 2; break;
+    case NSLI_F32: h->elem_bytes = 4; h->epv = 4; break;
+    case NSLI_BF16: h->elem_bytes = 2; h->epv = 8; break;
+    case NSLI_FP8E4M3: h->elem_bytes = 1; h->epv = 16; break;
+    default: return set_err(h, NSLI_ERR_ARG, "unknown storage type");
+    }
+    h->ld = round_up(h->n, h->epv);
+    h->row_bytes = (int)(h->ld * h->elem_bytes);
+    h->nv = h->row_bytes / 16;
+    const int vlim = map_vpt_limit(h->storage);
+    h->vpt = 0;
+    for (int v = 1; v <= vlim; v *= 2) {
+        if ((h->nv + v - 1) / v <= kMapMaxConsumers) {
+            h->vpt = v;
+            break;
+        }
+    }
+    if (h->vpt == 0)
+        return set_err(h, NSLI_ERR_UNSUPPORTED,
+                       "n too large for the register-resident row kernel of this build");
+    h->consumers = (int)round_up((h->nv + h->vpt - 1) / h->vpt, 32);
+    h->R = std::max(1, std::min(64, 65536 / h->row_bytes));
+    h->stage_stride = (int)round_up((long long)h->R * h->row_bytes + (long long)h->R * 32, 128);
+    const int budget = 232448 - kSmemHeader;
+    h->nstage = std::min(8, budget / h->stage_stride);
+    if (h->nstage < 2)
+        return set_err(h, NSLI_ERR_UNSUPPORTED, "row does not fit two shared-memory stages");
+    h->smem = (size_t)kSmemHeader + (size_t)h->nstage * h->stage_stride;
+    h->G = (int)std::min<long long>(h->num_sms, h->m);
+    h->rows_base = h->m / h->G;
+    h->rows_rem = (int)(h->m % h->G);
+    h->red_grid = (int)((h->ld + kReduceCols - 1) / kReduceCols);
+    return NSLI_OK;
+}
+
+MapArgs map_args(nsli_solver *h)
+{
+    MapArgs a;
+    a.A = h->A;
+    a.meta = h->meta;
+    a.x = h->x;
+    a.part_y = h->part_y;
+    a.part_stat = h->part_stat;
+    a.st = h->st;
+    a.ld = h->ld;
+    a.m = h->m;
+    a.rows_base = h->rows_base;
+    a.rows_rem = h->rows_rem;
+    a.nv = h->nv;
+    a.row_bytes = h->row_bytes;
+    a.rows_per_slot = h->R;
+    a.nstage = h->nstage;
+    a.stage_stride = h->stage_stride;
+    a.ignore_done = 0;
+    return a;
+}
+
+ReduceArgs reduce_args(nsli_solver *h)
+{
+    ReduceArgs a;
+    a.part_y = h->part_y;
+    a.part_stat = h->part_stat;
+    a.x = h->x;
+    a.ybuf = h->ybuf;
+    a.part_dx = h->part_dx;
+    a.st = h->st;
+    a.ld = h->ld;
+    a.G = h->G;
+    return a;
+}
+
+cudaError_t launch_iteration(nsli_solver *h)
+{
+    cudaError_t e = map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, map_args(h));
+    if (e != cudaSuccess)
+        return e;
+    return reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
+}
+
+int ensure_graph(nsli_solver *h, int iters)
+{
+    if (h->graph && h->graph_iters == iters)
+        return NSLI_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < iters && err == cudaSuccess; ++i)
+        err = launch_iteration(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (err != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        return cuda_err(h, err, "capture iteration block");
+    }
+    CK(e2, "end capture");
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e3, "instantiate iteration graph");
+    h->graph_iters = iters;
+    return NSLI_OK;
+}
+
+int validate_params(nsli_solver *h, const nsli_params *p)
+{
+    if (!p)
+        return set_err(h, NSLI_ERR_ARG, "params is NULL");
+    if (!(p->lambda > 0.0) || !std::isfinite(p->lambda))
+        return set_err(h, NSLI_ERR_ARG, "lambda must be finite and > 0");
+    if (p->rule != NSLI_RULE_RELAXED && p->rule != NSLI_RULE_MODAP)
+        return set_err(h, NSLI_ERR_ARG, "unknown rule");
+    if (p->stop < NSLI_STOP_NONE || p->stop > NSLI_STOP_MAXVIOL_REL)
+        return set_err(h, NSLI_ERR_ARG, "unknown stop rule");
+    if (!(p->eps >= 0.0) || !std::isfinite(p->eps))
+        return set_err(h, NSLI_ERR_ARG, "eps must be finite and >= 0");
+    if (p->max_iter < 0 || p->block_iters < 0 || p->block_iters > 4096 || p->reserved != 0)
+        return set_err(h, NSLI_ERR_ARG, "bad max_iter / block_iters / reserved");
+    if (!std::isfinite(p->rho))
+        return set_err(h, NSLI_ERR_ARG, "rho must be finite");
+    return NSLI_OK;
+}
+
+int read_flags(nsli_solver *h)
+{
+    CK(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    const int f = *h->flags_host;
+    if (f & PREPF_NONFINITE)
+        return set_err(h, NSLI_ERR_NONFINITE, "NaN or Inf in the input");
+    if (f & PREPF_ZERO_ROW)
+        return set_err(h, NSLI_ERR_ZERO_ROW, "A has a zero row (the method needs a_i != 0)");
+    return NSLI_OK;
+}
+
+double ord_dec(unsigned long long u)
+{
+    unsigned long long bits = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    double d;
+    std::memcpy(&d, &bits, sizeof d);
+    return d;
+}
+
+// Binary64 check at the current x and tick; fills h->last_check fields.
+int run_verify(nsli_solver *h)
+{
+    CK(cudaMemsetAsync(h->ver, 0, sizeof(VerOut), h->stream), "clear check");
+    VerifyArgs a;
+    a.A = h->A;
+    a.x = h->x;
+    a.b0_64 = h->b0_64;
+    a.av_64 = h->av_64;
+    a.n2_64 = h->n2_64;
+    a.scale = h->scale;
+    a.st = h->st;
+    a.out = h->ver;
+    a.ld = h->ld;
+    a.m = h->m;
+    a.nv = h->nv;
+    const int grid = std::max(1, std::min<int>(h->num_sms * 8, (int)((h->m + 7) / 8)));
+    CK(verify_launch(h->storage, grid, h->stream, a), "launch binary64 check");
+    h->launches += 1;
+    CK(cudaMemcpyAsync(h->ver_host, h->ver, sizeof(VerOut), cudaMemcpyDeviceToHost, h->stream), "read check");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    h->last_check.max_viol = ord_dec(h->ver_host->maxviol);
+    h->last_check.max_viol_norm = ord_dec(h->ver_host->maxnorm);
+    h->last_check.max_abs_b = ord_dec(h->ver_host->maxb);
+    h->last_check.h = (int64_t)h->ver_host->h;
+    return NSLI_OK;
+}
+
+int read_state(nsli_solver *h)
+{
+    CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    if (h->st_host->error & ERRF_TIMEOUT)
+        return set_err(h, NSLI_ERR_TIMEOUT, "a bounded device wait expired");
+    return NSLI_OK;
+}
+
+int begin_run(nsli_solver *h, const nsli_params *p, int stop, long long max_iter)
+{
+    StateBegin b;
+    b.lambda = p->lambda;
+    b.eps = p->eps;
+    b.rho = p->rho;
+    b.max_iter = max_iter;
+    b.rule = p->rule;
+    b.stop = stop;
+    b.reset_it = 1;
+    b.force_step = 0;
+    b.tick = -1;
+    CK(state_begin_launch(h->stream, h->st, b), "begin run");
+    h->launches += 1;
+    return NSLI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nsli_strerror(int code)
+{
+    switch (code) {
+    case NSLI_OK: return "ok";
+    case NSLI_NOT_CONVERGED: return "maximum number of iterations reached";
+    case NSLI_ERR_ARG: return "invalid argument";
+    case NSLI_ERR_ZERO_ROW: return "zero row in A";
+    case NSLI_ERR_NONFINITE: return "NaN or Inf in the input";
+    case NSLI_ERR_OOM: return "device memory allocation failed";
+    case NSLI_ERR_CUDA: return "CUDA runtime error";
+    case NSLI_ERR_TIMEOUT: return "bounded device wait expired";
+    case NSLI_ERR_UNSUPPORTED: return "outside the limits of this build";
+    default: return "unknown status";
+    }
+}
+
+const char *nsli_last_error(nsli_handle h) { return h ? h->last_error.c_str() : ""; }
+
+int64_t nsli_launch_count(nsli_handle h) { return h ? (int64_t)h->launches : 0; }
+
+int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t a_dtype, const void *A,
+                int64_t lda, const double *b0, const double *norms2, const double *Av, const double *x0,
+                void *stream)
+{
+    if (!out)
+        return NSLI_ERR_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || lda < n || !A || !b0 || !x0)
+        return NSLI_ERR_ARG;
+    if (a_dtype != NSLI_F32 && a_dtype != NSLI_F64)
+        return NSLI_ERR_ARG;
+    if (storage < NSLI_F64 || storage > NSLI_FP8E4M3)
+        return NSLI_ERR_ARG;
+    if ((storage == NSLI_BF16 || storage == NSLI_FP8E4M3) && a_dtype != NSLI_F32)
+        return NSLI_ERR_ARG;
+    if (m > (1ll << 40) || n > (1ll << 31))
+        return NSLI_ERR_UNSUPPORTED;
+
+    nsli_solver *h = new nsli_solver();
+    h->storage = storage;
+    h->m = m;
+    h->n = n;
+    int rc = NSLI_OK;
+    auto fail = [&](int code) {
+        free_all(h);
+        delete h;
+        return code;
+    };
+#define CKC(call, what)                                                                                      \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return fail(cuda_err(h, e_, what));                                                              \
+    } while (0)
+
+    CKC(cudaGetDevice(&h->device), "get device");
+    CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+    if ((rc = choose_config(h)) != NSLI_OK)
+        return fail(rc);
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CKC(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "create stream");
+        h->own_stream = true;
+    }
+    cudaStream_t s = h->stream;
+
+    const size_t accb = (storage == NSLI_F64) ? 8 : 4;
+    const size_t meta_bytes = 32;
+    CKC(cudaMalloc(&h->A, (size_t)m * h->row_bytes), "allocate A");
+    CKC(cudaMalloc(&h->meta, (size_t)m * meta_bytes), "allocate row records");
+    CKC(cudaMalloc((void **)&h->b0_64, (size_t)m * 8), "allocate b0");
+    CKC(cudaMalloc((void **)&h->av_64, (size_t)m * 8), "allocate Av");
+    CKC(cudaMalloc((void **)&h->n2_64, (size_t)m * 8), "allocate norms");
+    if (storage == NSLI_FP8E4M3)
+        CKC(cudaMalloc((void **)&h->scale, (size_t)m * 4), "allocate row scales");
+    CKC(cudaMalloc(&h->x, (size_t)h->ld * accb), "allocate x");
+    CKC(cudaMalloc(&h->part_y, (size_t)h->G * h->ld * accb), "allocate partial sums");
+    CKC(cudaMalloc((void **)&h->part_stat, (size_t)h->G * sizeof(PartStat)), "allocate partial stats");
+    CKC(cudaMalloc((void **)&h->part_dx, (size_t)h->red_grid * 8), "allocate step partials");
+    CKC(cudaMalloc((void **)&h->ybuf, (size_t)h->ld * 8), "allocate y");
+    CKC(cudaMalloc((void **)&h->dtmp, (size_t)std::max<long long>(m, h->ld) * 8), "allocate staging");
+    CKC(cudaMalloc((void **)&h->st, sizeof(DevState)), "allocate state");
+    CKC(cudaMalloc((void **)&h->ver, sizeof(VerOut)), "allocate check");
+    CKC(cudaMalloc((void **)&h->flags, sizeof(int)), "allocate flags");
+    CKC(cudaMallocHost((void **)&h->st_host, sizeof(DevState)), "allocate pinned state");
+    CKC(cudaMallocHost((void **)&h->ver_host, sizeof(VerOut)), "allocate pinned check");
+    CKC(cudaMallocHost((void **)&h->flags_host, sizeof(int)), "allocate pinned flags");
+
+    CKC(cudaMemsetAsync(h->st, 0, sizeof(DevState), s), "clear state");
+    CKC(cudaMemsetAsync(h->flags, 0, sizeof(int), s), "clear flags");
+    CKC(cudaMemsetAsync(h->ybuf, 0, (size_t)h->ld * 8, s), "clear y");
+    CKC(cudaMemcpyAsync(h->b0_64, b0, (size_t)m * 8, cudaMemcpyDefault, s), "copy b0");
+    if (Av)
+        CKC(cudaMemcpyAsync(h->av_64, Av, (size_t)m * 8, cudaMemcpyDefault, s), "copy Av");
+    else
+        CKC(cudaMemsetAsync(h->av_64, 0, (size_t)m * 8, s), "clear Av");
+    CKC(check_finite_launch(s, h->b0_64, m, h->flags), "check b0");
+    CKC(check_finite_launch(s, h->av_64, m, h->flags), "check Av");
+    h->launches += 2;
+
+    // x0 -> accumulation type (the staging buffer is reused for the norms
+    // only after this kernel has consumed it, in stream order)
+    CKC(cudaMemcpyAsync(h->dtmp, x0, (size_t)n * 8, cudaMemcpyDefault, s), "copy x0");
+    CKC(x_from_f64_launch(storage == NSLI_F64, s, h->dtmp, h->x, n, h->ld, h->flags), "convert x0");
+    h->launches += 1;
+
+    const double *norms_dev = nullptr;
+    double *norms_buf = nullptr;
+    if (norms2) {
+        CKC(cudaMalloc((void **)&norms_buf, (size_t)m * 8), "allocate norms input");
+        cudaError_t e = cudaMemcpyAsync(norms_buf, norms2, (size_t)m * 8, cudaMemcpyDefault, s);
+        if (e != cudaSuccess) {
+            cudaFree(norms_buf);
+            return fail(cuda_err(h, e, "copy norms"));
+        }
+        norms_dev = norms_buf;
+    }
+
+    // A: quantise / copy row blocks into the padded device layout
+    const size_t src_eb = (a_dtype == NSLI_F64) ? 8 : 4;
+    const bool a_on_device = is_device_ptr(A);
+    long long chunk = std::max<long long>(1, (256ll << 20) / (long long)(lda * src_eb));
+    chunk = std::min<long long>(chunk, m);
+    void *stage = nullptr;
+    if (!a_on_device) {
+        cudaError_t e = cudaMalloc(&stage, (size_t)chunk * lda * src_eb);
+        if (e != cudaSuccess) {
+            if (norms_buf)
+                cudaFree(norms_buf);
+            return fail(cuda_err(h, e, "allocate staging for A"));
+        }
+    }
+    cudaError_t err = cudaSuccess;
+    for (long long r0 = 0; r0 < m && err == cudaSuccess; r0 += chunk) {
+        const long long rows = std::min(chunk, m - r0);
+        PrepArgs pa;
+        if (a_on_device) {
+            pa.src = static_cast<const unsigned char *>(A) + (size_t)r0 * lda * src_eb;
+        } else {
+            err = cudaMemcpy2DAsync(stage, (size_t)lda * src_eb,
+                                    static_cast<const unsigned char *>(A) + (size_t)r0 * lda * src_eb,
+                                    (size_t)lda * src_eb, (size_t)n * src_eb, (size_t)rows, cudaMemcpyDefault, s);
+            if (err != cudaSuccess)
+                break;
+            pa.src = stage;
+        }
+        pa.lda = lda;
+        pa.src_f64 = (a_dtype == NSLI_F64) ? 1 : 0;
+        pa.A = h->A;
+        pa.ld = h->ld;
+        pa.n = n;
+        pa.row0 = r0;
+        pa.rows = rows;
+        pa.norms_in = norms_dev;
+        pa.n2_64 = h->n2_64;
+        pa.scale = h->scale;
+        pa.flags = h->flags;
+        err = prep_launch(storage, s, pa);
+        h->launches += 1;
+        if (!a_on_device && err == cudaSuccess)
+            err = cudaStreamSynchronize(s);  // the staging buffer is reused
+    }
+    if (err == cudaSuccess) {
+        MetaArgs ma;
+        ma.meta = h->meta;
+        ma.b0_64 = h->b0_64;
+        ma.av_64 = h->av_64;
+        ma.n2_64 = h->n2_64;
+        ma.scale = h->scale;
+        ma.m = m;
+        ma.flags = h->flags;
+        err = meta_launch(storage == NSLI_F64, s, ma);
+        h->launches += 1;
+    }
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(s);
+    if (stage)
+        cudaFree(stage);
+    if (norms_buf)
+        cudaFree(norms_buf);
+    if (err != cudaSuccess)
+        return fail(cuda_err(h, err, "prepare A"));
+    if ((rc = read_flags(h)) != NSLI_OK)
+        return fail(rc);
+    CKC(map_prepare(storage, h->vpt, h->smem), "configure Map kernel");
+#undef CKC
+    *out = h;
+    return NSLI_OK;
+}
+
+void nsli_destroy(nsli_handle h)
+{
+    if (!h)
+        return;
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int nsli_sync(nsli_handle h)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return NSLI_OK;
+}
+
+int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    if (b0) {
+        CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream), "clear flags");
+        CK(cudaMemcpyAsync(h->b0_64, b0, (size_t)h->m * 8, cudaMemcpyDefault, h->stream), "copy b0");
+        MetaArgs ma;
+        ma.meta = h->meta;
+        ma.b0_64 = h->b0_64;
+        ma.av_64 = h->av_64;
+        ma.n2_64 = h->n2_64;
+        ma.scale = h->scale;
+        ma.m = h->m;
+        ma.flags = h->flags;
+        CK(meta_launch(h->storage == NSLI_F64, h->stream, ma), "update row records");
+        h->launches += 1;
+    }
+    if (tick >= 0) {
+        const long long t = tick;  // pageable source: staged before the call returns
+        CK(cudaMemcpyAsync(&h->st->tick, &t, sizeof t, cudaMemcpyHostToDevice, h->stream), "set tick");
+    }
+    if (b0)
+        return read_flags(h);
+    return NSLI_OK;
+}
+
+int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    int rc = validate_params(h, p);
+    if (rc != NSLI_OK)
+        return rc;
+    if (n_iter < 0)
+        return set_err(h, NSLI_ERR_ARG, "n_iter < 0");
+    if ((rc = begin_run(h, p, NSLI_STOP_NONE, LLONG_MAX)) != NSLI_OK)
+        return rc;
+    const int B = p->block_iters > 0 ? p->block_iters : 32;
+    const long long full = n_iter / B;
+    const long long rem = n_iter % B;
+    if (full > 0) {
+        if ((rc = ensure_graph(h, B)) != NSLI_OK)
+            return rc;
+        for (long long i = 0; i < full; ++i) {
+            CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
+            h->launches += 2ll * B;
+        }
+    }
+    for (long long i = 0; i < rem; ++i) {
+        CK(launch_iteration(h), "launch iteration");
+        h->launches += 2;
+    }
+    return NSLI_OK;
+}
+
+int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter, double *kernel_ms)
+{
+    if (!h || !kernel_ms)
+        return NSLI_ERR_ARG;
+    int rc = validate_params(h, p);
+    if (rc != NSLI_OK)
+        return rc;
+    if (n_iter < 0 || n_iter > 100000)
+        return set_err(h, NSLI_ERR_ARG, "n_iter out of range for the timed run");
+    if ((rc = begin_run(h, p, NSLI_STOP_NONE, LLONG_MAX)) != NSLI_OK)
+        return rc;
+    kernel_ms[0] = 0.0;
+    kernel_ms[1] = 0.0;
+    const int batch = 64;  // iterations per event batch
+    cudaEvent_t ev[3 * batch];
+    for (int i = 0; i < 3 * batch; ++i)
+        CK(cudaEventCreate(&ev[i]), "create event");
+    cudaError_t err = cudaSuccess;
+    for (long long done = 0; done < n_iter && err == cudaSuccess; done += batch) {
+        const int cnt = (int)std::min<long long>(batch, n_iter - done);
+        for (int i = 0; i < cnt && err == cudaSuccess; ++i) {
+            cudaEventRecord(ev[3 * i], h->stream);
+            err = map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, map_args(h));
+            if (err != cudaSuccess)
+                break;
+            cudaEventRecord(ev[3 * i + 1], h->stream);
+            err = reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
+            cudaEventRecord(ev[3 * i + 2], h->stream);
+            h->launches += 2;
+        }
+        if (err == cudaSuccess)
+            err = cudaStreamSynchronize(h->stream);
+        for (int i = 0; i < cnt && err == cudaSuccess; ++i) {
+            float a = 0.f, b = 0.f;
+            err = cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+            if (err == cudaSuccess)
+                err = cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+            kernel_ms[0] += a;
+            kernel_ms[1] += b;
+        }
+    }
+    for (int i = 0; i < 3 * batch; ++i)
+        cudaEventDestroy(ev[i]);
+    CK(err, "timed iterations");
+    return read_state(h);
+}
+
+int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    int rc = validate_params(h, p);
+    if (rc != NSLI_OK)
+        return rc;
+    if ((rc = begin_run(h, p, p->stop, p->max_iter)) != NSLI_OK)
+        return rc;
+    const int B = p->block_iters > 0 ? p->block_iters : 32;
+    if ((rc = ensure_graph(h, B)) != NSLI_OK)
+        return rc;
+    int status = NSLI_NOT_CONVERGED;
+    // every block either makes B updates or ends the run; a rejected
+    // candidate forces one update, so this bound is never reached
+    const long long max_blocks = p->max_iter / B + p->max_iter + 4;
+    bool finished = false;
+    for (long long blk = 0; blk < max_blocks && !finished; ++blk) {
+        CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
+        h->launches += 2ll * B;
+        if ((rc = read_state(h)) != NSLI_OK)
+            return rc;
+        const int sst = h->st_host->status;
+        if (sst == ST_RUNNING)
+            continue;
+        if (sst == ST_CANDIDATE) {
+            if ((rc = run_verify(h)) != NSLI_OK)
+                return rc;
+            bool accept;
+            if (p->stop == NSLI_STOP_EPSMEM)
+                accept = h->last_check.max_viol_norm < p->eps;
+            else if (p->stop == NSLI_STOP_MAXVIOL_REL)
+                accept = h->last_check.max_viol <= p->eps * h->last_check.max_abs_b;
+            else
+                accept = h->last_check.h == 0;
+            if (accept) {
+                status = NSLI_OK;
+                finished = true;
+            } else {
+                CK(state_resume_launch(h->stream, h->st), "resume");
+                h->launches += 1;
+            }
+            continue;
+        }
+        status = sst;  // NSLI_OK (step rule) or NSLI_NOT_CONVERGED
+        finished = true;
+    }
+    if ((rc = read_state(h)) != NSLI_OK)
+        return rc;
+    if ((rc = run_verify(h)) != NSLI_OK)
+        return rc;
+    nsli_result r = h->last_check;
+    r.iters = h->st_host->it;
+    r.tick = h->st_host->tick;
+    r.status = status;
+    r.last_step_norm = h->st_host->dx_norm;
+    h->last_check = r;
+    if (out)
+        *out = r;
+    return status;
+}
+
+int nsli_residual_max(nsli_handle h, double *max_viol, double *max_viol_norm)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    int rc = run_verify(h);
+    if (rc != NSLI_OK)
+        return rc;
+    if (max_viol)
+        *max_viol = h->last_check.max_viol;
+    if (max_viol_norm)
+        *max_viol_norm = h->last_check.max_viol_norm;
+    return NSLI_OK;
+}
+
+int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    MapArgs ma = map_args(h);
+    ma.ignore_done = 1;  // also after a finished run
+    CK(map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
+    CK(reduce_only_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h), h->ybuf),
+       "launch Reduce");
+    h->launches += 2;
+    if (y)
+        CK(cudaMemcpyAsync(y, h->ybuf, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy y");
+    int rc = read_state(h);
+    if (rc != NSLI_OK)
+        return rc;
+    if (violated)
+        *violated = h->st_host->h;
+    if (stats) {
+        stats[0] = h->st_host->maxviol;
+        stats[1] = h->st_host->maxnorm;
+        stats[2] = h->st_host->maxb;
+    }
+    return NSLI_OK;
+}
+
+int nsli_get_x(nsli_handle h, double *x)
+{
+    if (!h || !x)
+        return NSLI_ERR_ARG;
+    CK(x_to_f64_launch(h->storage == NSLI_F64, h->stream, h->x, h->dtmp, h->n), "convert x");
+    h->launches += 1;
+    CK(cudaMemcpyAsync(x, h->dtmp, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return NSLI_OK;
+}
+
+int nsli_set_x(nsli_handle h, const double *x)
+{
+    if (!h || !x)
+        return NSLI_ERR_ARG;
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream), "clear flags");
+    CK(cudaMemcpyAsync(h->dtmp, x, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
+    CK(x_from_f64_launch(h->storage == NSLI_F64, h->stream, h->dtmp, h->x, h->n, h->ld, h->flags), "convert x");
+    h->launches += 1;
+    return read_flags(h);
+}
+
+int nsli_get_stored_rows(nsli_handle h, int64_t row0, int64_t rows, double *out)
+{
+    if (!h || !out || row0 < 0 || rows < 0 || row0 + rows > h->m)
+        return NSLI_ERR_ARG;
+    if (rows == 0)
+        return NSLI_OK;
+    double *tmp = nullptr;
+    CK(cudaMalloc((void **)&tmp, (size_t)rows * h->n * 8), "allocate row copy");
+    cudaError_t e = stored_rows_launch(h->storage, h->stream, h->A, h->scale, h->ld, h->n, row0, rows, tmp);
+    h->launches += 1;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, tmp, (size_t)rows * h->n * 8, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    CK(e, "copy stored rows");
+    return NSLI_OK;
+}
+
+int nsli_get_norms2(nsli_handle h, double *out)
+{
+    if (!h || !out)
+        return NSLI_ERR_ARG;
+    CK(cudaMemcpyAsync(out, h->n2_64, (size_t)h->m * 8, cudaMemcpyDefault, h->stream), "copy norms");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return NSLI_OK;
+}
+
+int nsli_get_result(nsli_handle h, nsli_result *out)
+{
+    if (!h || !out)
+        return NSLI_ERR_ARG;
+    int rc = read_state(h);
+    if (rc != NSLI_OK)
+        return rc;
+    nsli_result r = h->last_check;
+    r.iters = h->st_host->it;
+    r.tick = h->st_host->tick;
+    const int sst = h->st_host->status;
+    r.status = (sst == ST_RUNNING || sst == ST_CANDIDATE) ? NSLI_NOT_CONVERGED : sst;
+    r.last_step_norm = h->st_host->dx_norm;
+    *out = r;
+    return NSLI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// nsli_internal.h -- layouts shared by the host library and the kernels.
+//
+// Device layout of one problem (all buffers owned by the handle):
+//   A      m rows x ld elements of the storage type, row-major, each row
+//          zero-padded from n to ld so that a row is a whole number of
+//          16-byte vectors (the unit of the bulk copies and of the loads).
+//   meta   one 32-byte record per row: b0_i, (Av)_i, 1/||a_i||^2, 1/||a_i||
+//          and the FP8 row scale, in the accumulation type; the Map streams
+//          it beside the row.
+//   b0_64, av_64, n2_64   binary64 copies for the binary64 check.
+//   x      ld elements of the accumulation type (padding stays zero).
+//   part_y G x ld partial sums of the positive slices, one row per CTA of
+//          the Map; part_stat G records (h, max r, max r/||a||, max |b|).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nsli {
+
+struct RowMeta32 {
+    float b0, av, inv_n2, inv_n, scale, pad0, pad1, pad2;
+};
+struct RowMeta64 {
+    double b0, av, inv_n2, inv_n;
+};
+static_assert(sizeof(RowMeta32) == 32, "row record is 32 bytes");
+static_assert(sizeof(RowMeta64) == 32, "row record is 32 bytes");
+
+struct PartStat {
+    long long h;
+    double maxviol, maxnorm, maxb;
+};
+
+// Device-resident state of the iteration; the kernels read the control
+// fields at run time so one captured graph serves every solve.
+struct DevState {
+    // control, written by the host before a run
+    double lambda, eps, rho;
+    long long max_iter;   // absolute bound on `it`
+    int rule, stop, force_step, pad0;
+    // progress, written by the kernels
+    long long it;         // x-updates performed in this run
+    long long tick;       // k of b(k)
+    int done;             // non-zero: every kernel returns at once
+    int status;           // ST_RUNNING, ST_CANDIDATE, 0 = OK, 1 = NOT_CONVERGED
+    int error;            // ERRF_* bits
+    unsigned int ticket;  // last-block counter of the reduce kernel
+    long long h;          // stats of the last Map
+    double maxviol, maxnorm, maxb, dx_norm, y_norm;
+};
+
+enum : int { ST_RUNNING = 2, ST_CANDIDATE = 3 };
+enum : int { ERRF_TIMEOUT = 1 };
+enum : int { PREPF_ZERO_ROW = 1, PREPF_NONFINITE = 2 };
+
+// Result of the binary64 check: maxima kept as order-preserving integers.
+struct VerOut {
+    unsigned long long maxviol, maxnorm, maxb;
+    unsigned long long h;
+};
+
+struct MapArgs {
+    const void *A;
+    const void *meta;
+    const void *x;
+    void *part_y;
+    PartStat *part_stat;
+    DevState *st;
+    long long ld;          // elements per stored row
+    long long m;
+    long long rows_base;   // rows per CTA = rows_base (+1 for the first rows_rem)
+    int rows_rem;
+    int nv;                // 16-byte vectors per stored row
+    int row_bytes;
+    int rows_per_slot;     // R
+    int nstage;
+    int stage_stride;      // bytes per stage in shared memory
+    int ignore_done;       // run even when the done flag is set
+};
+
+struct ReduceArgs {
+    const void *part_y;
+    const PartStat *part_stat;
+    void *x;
+    double *ybuf;
+    double *part_dx;
+    DevState *st;
+    long long ld;
+    int G;
+};
+
+struct VerifyArgs {
+    const void *A;
+    const void *x;
+    const double *b0_64, *av_64, *n2_64;
+    const float *scale;    // per-row FP8 scale (NULL otherwise)
+    const DevState *st;
+    VerOut *out;
+    long long ld, m;
+    int nv;
+};
+
+// ---- launchers (nsli_kernels.cu) -------------------------------------------
+constexpr int kMapMaxConsumers = 512;
+constexpr int kMapRowGroup = 4;      // rows reduced per block barrier
+constexpr int kReduceCols = 32;      // columns per reduce block
+constexpr int kSmemHeader = 2304;    // barriers, flags, warp-sum buffers
+
+int map_vpt_limit(int storage);      // largest vectors-per-thread instance
+cudaError_t map_prepare(int storage, int vpt, size_t smem);
+cudaError_t map_launch(int storage, int vpt, int grid, int consumers, size_t smem,
+                       cudaStream_t s, const MapArgs &a);
+cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a);
+cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a,
+                               double *y_out);
+cudaError_t verify_launch(int storage, int grid, cudaStream_t s, const VerifyArgs &a);
+
+struct PrepArgs {
+    const void *src;        // staged source rows (device), row pitch lda
+    long long lda;
+    int src_f64;
+    void *A;                // destination rows (storage type), pitch ld
+    long long ld, n;
+    long long row0, rows;   // rows of this launch (global index row0)
+    const double *norms_in; // optional user norms (global index)
+    double *n2_64;
+    float *scale;           // FP8 row scale (global index) or NULL
+    int *flags;
+};
+cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a);
+
+struct MetaArgs {
+    void *meta;
+    const double *b0_64, *av_64, *n2_64;
+    const float *scale;
+    long long m;
+    int *flags;
+};
+cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a);
+
+cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, void *x,
+                              long long n, long long ld, int *flags);
+cudaError_t x_to_f64_launch(bool f64, cudaStream_t s, const void *x, double *dst, long long n);
+cudaError_t check_finite_launch(cudaStream_t s, const double *v, long long n, int *flags);
+
+struct StateBegin {
+    double lambda, eps, rho;
+    long long max_iter;
+    int rule, stop;
+    int reset_it;        // 1: it = 0
+    int force_step;
+    long long tick;      // >= 0: set the tick
+};
+cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b);
+cudaError_t state_resume_launch(cudaStream_t s, DevState *st);
+cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
+                               long long n, long long row0, long long rows, double *out);
+
+}  // namespace nsli

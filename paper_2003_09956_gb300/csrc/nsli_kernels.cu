@@ -1,0 +1,1077 @@
+// nsli_kernels.cu -- device code of the pseudo-projection solver (sm_103a).
+//
+// Kernels of one iteration (Sokolinsky & Sokolinskaya 2020):
+//   map_kernel     Map of Eq. 13 fused with the CTA-level Reduce(+): streams
+//                  the CTA's contiguous block of rows of A once through a
+//                  shared-memory ring filled by the bulk-copy (TMA) engine,
+//                  forms r_i = <a_i, x> - b_i(k) with b_i(k) = b0_i + k rho Av_i
+//                  (Section 5 tick, never materialised), and while the row is
+//                  still on chip adds the positive slice (Eq. 7)
+//                  r_i / ||a_i||^2 * a_i into register-resident partial sums.
+//   reduce_update  deterministic fixed-order sum of the per-CTA partials,
+//                  the stopping test (Eq. 10 and the step rule), and the step
+//                  x <- x - lambda y / h (Eq. 8) or x <- x - lambda y / ||y||
+//                  (Eq. 12), with ||dx|| in binary64.
+// Plus the set-up kernels (quantisation of A, binary64 row norms, per-row
+// records) and the binary64 feasibility check (Eq. 10 on the stored A).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cfloat>
+#include <cmath>
+
+#include "nsli.h"
+#include "nsli_internal.h"
+
+namespace nsli {
+
+// ---------------------------------------------------------------- traits ----
+
+template <int S> struct Traits;
+template <> struct Traits<NSLI_F64> {
+    using acc = double;
+    using meta = RowMeta64;
+    static constexpr int EPV = 2;   // elements per 16-byte vector
+    static constexpr int BYTES = 8;
+};
+template <> struct Traits<NSLI_F32> {
+    using acc = float;
+    using meta = RowMeta32;
+    static constexpr int EPV = 4;
+    static constexpr int BYTES = 4;
+};
+template <> struct Traits<NSLI_BF16> {
+    using acc = float;
+    using meta = RowMeta32;
+    static constexpr int EPV = 8;
+    static constexpr int BYTES = 2;
+};
+template <> struct Traits<NSLI_FP8E4M3> {
+    using acc = float;
+    using meta = RowMeta32;
+    static constexpr int EPV = 16;
+    static constexpr int BYTES = 1;
+};
+
+__device__ __forceinline__ float meta_scale(const RowMeta32 &m) { return m.scale; }
+__device__ __forceinline__ double meta_scale(const RowMeta64 &) { return 1.0; }
+
+__device__ __forceinline__ void fp8x2_to_float2(unsigned int pair, float &lo, float &hi)
+{
+    __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(pair & 0xffffu), __NV_E4M3);
+    const float2 f = __half22float2(__half2(hr));
+    lo = f.x;
+    hi = f.y;
+}
+
+// Decode one 16-byte vector of stored elements into the accumulation type.
+template <int S>
+__device__ __forceinline__ void decode(const uint4 q, typename Traits<S>::acc (&a)[Traits<S>::EPV]);
+
+template <> __device__ __forceinline__ void decode<NSLI_F64>(const uint4 q, double (&a)[2])
+{
+    a[0] = __hiloint2double((int)q.y, (int)q.x);
+    a[1] = __hiloint2double((int)q.w, (int)q.z);
+}
+template <> __device__ __forceinline__ void decode<NSLI_F32>(const uint4 q, float (&a)[4])
+{
+    a[0] = __uint_as_float(q.x);
+    a[1] = __uint_as_float(q.y);
+    a[2] = __uint_as_float(q.z);
+    a[3] = __uint_as_float(q.w);
+}
+template <> __device__ __forceinline__ void decode<NSLI_BF16>(const uint4 q, float (&a)[8])
+{
+    const unsigned int w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[2 * k] = __uint_as_float(w[k] << 16);
+        a[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <> __device__ __forceinline__ void decode<NSLI_FP8E4M3>(const uint4 q, float (&a)[16])
+{
+    const unsigned int w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        fp8x2_to_float2(w[k], a[4 * k], a[4 * k + 1]);
+        fp8x2_to_float2(w[k] >> 16, a[4 * k + 2], a[4 * k + 3]);
+    }
+}
+
+// ------------------------------------------------ barriers and bulk copies --
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned int smem_u32(const void *p)
+{
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned int bar, unsigned int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned int bar, unsigned int bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned int bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned int bar, unsigned int parity)
+{
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete; gives up after the
+// time limit or when *abort_flag becomes non-zero.  Returns true on success.
+__device__ __noinline__ bool mbar_wait_bounded(unsigned int bar, unsigned int parity,
+                                               volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (abort_flag != nullptr && *abort_flag)
+            return false;
+        if (gtimer() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(unsigned int dst, const void *src, unsigned int bytes,
+                                         unsigned int bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// Block barrier (id 1) with an OR-vote, so that every thread leaves the
+// loop together when any of them gave up waiting.
+__device__ __forceinline__ int bar_all_or(int nthreads, int pred)
+{
+    unsigned int out;
+    asm volatile(
+        "{\n\t.reg .pred q, p;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(out)
+        : "r"(pred), "r"(nthreads)
+        : "memory");
+    return (int)out;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T neg_inf();
+template <> __device__ __forceinline__ float neg_inf<float>() { return -INFINITY; }
+template <> __device__ __forceinline__ double neg_inf<double>() { return -INFINITY; }
+
+// ------------------------------------------------------------- Map kernel --
+//
+// Block = `nt` threads (a multiple of 32, at most 512).  Thread t owns the
+// 16-byte vectors j = t + v * nt (v < VPT) of every row, i.e. fixed column
+// slices, and keeps the matching slices of x and of the CTA's partial y in
+// registers.  Thread 0 also issues the bulk copies: slots 0..nstage-1 up
+// front, then, right after the first barrier of slot s, the refill of the
+// stage that slot s-1 released (every warp released it before reaching that
+// barrier, so the wait is immediate).
+// Per group of up to 4 rows: per-thread partial dots, warp butterfly, one
+// barrier, every thread sums the warp totals in the same order (so all
+// threads hold bit-identical r_i), then the violated rows are added into
+// the y registers from the same shared-memory copy of the row.
+template <int S, int VPT>
+__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs p)
+{
+    using Tr = Traits<S>;
+    using Acc = typename Tr::acc;
+    using Meta = typename Tr::meta;
+    constexpr int EPV = Tr::EPV;
+    // rows per barrier: fewer when a thread already holds 32 row elements
+    constexpr int RG = (VPT * EPV >= 32) ? 2 : kMapRowGroup;
+
+    DevState *st = p.st;
+    if (!p.ignore_done && *(volatile int *)&st->done)
+        return;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);  // full[8], empty[8]
+    Acc *red = reinterpret_cast<Acc *>(smem + 256);                          // [2][RG][32]
+    unsigned char *stages = smem + kSmemHeader;
+
+    const int tid = threadIdx.x;
+    const int nt = (int)blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nwarps = nt >> 5;
+
+    const long long b = blockIdx.x;
+    const long long row_begin = b * p.rows_base + (b < p.rows_rem ? b : (long long)p.rows_rem);
+    const long long row_end = row_begin + p.rows_base + (b < p.rows_rem ? 1 : 0);
+    const int R = p.rows_per_slot;
+    const int nslots = (int)((row_end - row_begin + R - 1) / R);
+    const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
+    const unsigned char *Mb = static_cast<const unsigned char *>(p.meta);
+
+    // issue the copies of slot s into its stage (thread 0 only)
+    auto issue = [&](int s) {
+        const int stage = s % p.nstage;
+        const long long r0 = row_begin + (long long)s * R;
+        const long long left = row_end - r0;
+        const int rows = (int)(left < R ? left : R);
+        const unsigned int bytesA = (unsigned int)rows * (unsigned int)p.row_bytes;
+        const unsigned int bytesM = (unsigned int)rows * 32u;
+        unsigned char *dst = stages + (size_t)stage * p.stage_stride;
+        const unsigned int fb = smem_u32(&bars[stage]);
+        mbar_expect_tx(fb, bytesA + bytesM);
+        bulk_g2s(smem_u32(dst), Ab + r0 * (long long)p.row_bytes, bytesA, fb);
+        bulk_g2s(smem_u32(dst + (size_t)R * p.row_bytes), Mb + r0 * 32, bytesM, fb);
+    };
+
+    int issued = 0;
+    if (tid == 0) {
+        for (int s = 0; s < p.nstage; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1u);
+            mbar_init(smem_u32(&bars[8 + s]), (unsigned int)nwarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int first = nslots < p.nstage ? nslots : p.nstage;
+        for (int s = 0; s < first; ++s)
+            issue(s);
+        issued = first;
+    }
+    __syncthreads();
+
+    Acc xr[VPT][EPV];
+    Acc yr[VPT][EPV];
+    {
+        const Acc *xg = static_cast<const Acc *>(p.x);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int j = tid + v * nt;
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                xr[v][e] = (j < p.nv) ? xg[(long long)j * EPV + e] : Acc(0);
+                yr[v][e] = Acc(0);
+            }
+        }
+    }
+    const Acc tk = (Acc)((double)st->tick * st->rho);
+
+    long long h_loc = 0;
+    Acc mv = neg_inf<Acc>(), mn = neg_inf<Acc>(), mb = Acc(0);
+    int grp_counter = 0;
+    int aborted = 0;
+    int consumed = 0;
+
+    for (int s = 0; s < nslots; ++s) {
+        const int stage = s % p.nstage;
+        const unsigned int ph = (unsigned int)((s / p.nstage) & 1);
+        int timed_out = mbar_wait_bounded(smem_u32(&bars[stage]), ph, nullptr) ? 0 : 1;
+        const unsigned char *sbase = stages + (size_t)stage * p.stage_stride;
+        const Meta *smeta = reinterpret_cast<const Meta *>(sbase + (size_t)R * p.row_bytes);
+        const long long r0 = row_begin + (long long)s * R;
+        const long long left = row_end - r0;
+        const int rows = (int)(left < R ? left : R);
+
+        for (int g0 = 0; g0 < rows; g0 += RG) {
+            const int gr = (rows - g0) < RG ? (rows - g0) : RG;
+            Acc acc[RG];
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                acc[rr] = Acc(0);
+                if (rr < gr) {
+                    const uint4 *rowv = reinterpret_cast<const uint4 *>(sbase + (size_t)(g0 + rr) * p.row_bytes);
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        const int j = tid + v * nt;
+                        if (j < p.nv) {
+                            Acc a[EPV];
+                            decode<S>(rowv[j], a);
+#pragma unroll
+                            for (int e = 0; e < EPV; ++e)
+                                acc[rr] = fma(a[e], xr[v][e], acc[rr]);
+                        }
+                    }
+                }
+            }
+            Acc *rb = red + (grp_counter & 1) * RG * 32;
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                if (rr < gr) {
+                    const Acc t = warp_sum(acc[rr]);
+                    if (lane == 0)
+                        rb[rr * 32 + warp] = t;
+                }
+            }
+            aborted = bar_all_or(nt, timed_out);
+            if (aborted)
+                break;
+            if (tid == 0 && g0 == 0 && s >= 1 && issued < nslots) {
+                // slot s-1 was released by every warp before this barrier
+                const int sp = s - 1;
+                if (mbar_wait_bounded(smem_u32(&bars[8 + sp % p.nstage]),
+                                      (unsigned int)((sp / p.nstage) & 1), nullptr)) {
+                    issue(issued);
+                    ++issued;
+                } else {
+                    timed_out = 1;  // reported at the next barrier
+                }
+            }
+
+            Acc c[RG];
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                c[rr] = Acc(0);
+                if (rr < gr) {
+                    Acc dot = Acc(0);
+                    for (int w = 0; w < nwarps; ++w)
+                        dot += rb[rr * 32 + w];
+                    const Meta md = smeta[g0 + rr];
+                    const Acc sc = (Acc)meta_scale(md);
+                    const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
+                    const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
+                    if (ri > Acc(0))
+                        c[rr] = (S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2;
+                    if (tid == 0) {
+                        h_loc += (ri > Acc(0)) ? 1 : 0;
+                        mv = ri > mv ? ri : mv;
+                        const Acc rn = ri * (Acc)md.inv_n;
+                        mn = rn > mn ? rn : mn;
+                        const Acc ab = bi < Acc(0) ? -bi : bi;
+                        mb = ab > mb ? ab : mb;
+                    }
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                if (rr < gr && c[rr] != Acc(0)) {
+                    const uint4 *rowv = reinterpret_cast<const uint4 *>(sbase + (size_t)(g0 + rr) * p.row_bytes);
+                    const Acc cr = c[rr];
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        const int j = tid + v * nt;
+                        if (j < p.nv) {
+                            Acc a[EPV];
+                            decode<S>(rowv[j], a);
+#pragma unroll
+                            for (int e = 0; e < EPV; ++e)
+                                yr[v][e] = fma(cr, a[e], yr[v][e]);
+                        }
+                    }
+                }
+            }
+            ++grp_counter;
+        }
+        if (aborted)
+            break;
+        // a refill wait that gave up is voted on at the next barrier; with no
+        // barrier left in this CTA it is reported directly
+        if (timed_out && tid == 0)
+            atomicOr(&st->error, ERRF_TIMEOUT);
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(smem_u32(&bars[8 + stage]));
+        consumed = s + 1;
+    }
+
+    if (aborted) {
+        // Give up: record the error and wait (bounded) for every bulk copy
+        // still in flight before the CTA exits.
+        if (tid == 0) {
+            atomicOr(&st->error, ERRF_TIMEOUT);
+            for (int s = consumed; s < issued; ++s)
+                mbar_wait_bounded(smem_u32(&bars[s % p.nstage]), (unsigned int)((s / p.nstage) & 1), nullptr);
+        }
+        return;
+    }
+
+    Acc *py = static_cast<Acc *>(p.part_y) + (long long)blockIdx.x * p.ld;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int j = tid + v * nt;
+        if (j < p.nv) {
+#pragma unroll
+            for (int e = 0; e < EPV; ++e)
+                py[(long long)j * EPV + e] = yr[v][e];
+        }
+    }
+    if (tid == 0) {
+        PartStat ps;
+        ps.h = h_loc;
+        ps.maxviol = (double)mv;
+        ps.maxnorm = (double)mn;
+        ps.maxb = (double)mb;
+        p.part_stat[blockIdx.x] = ps;
+    }
+}
+
+// ---------------------------------------------------- reduce and update ----
+//
+// Block = 256 threads = 8 groups x 32 columns.  Group q sums partial rows
+// g = q, q + 8, ... of its column in binary64; the 8 group sums are added in
+// order 0..7.  Every block recomputes h and the maxima from the per-CTA
+// records (exact integer sum / exact maxima), so all blocks take the same
+// decision.  The last block to finish (ticket) completes the step.
+struct ReduceShared {
+    double part[8][32];
+    double red[8];
+    long long h;
+    double mv, mn, mb;
+    int last;
+};
+
+__device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceShared &sh)
+{
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        long long h = 0;
+        double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+        for (int g = lane; g < G; g += 32) {
+            const PartStat q = ps[g];
+            h += q.h;
+            mv = fmax(mv, q.maxviol);
+            mn = fmax(mn, q.maxnorm);
+            mb = fmax(mb, q.maxb);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            h += __shfl_xor_sync(0xffffffffu, h, off);
+            mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+            mn = fmax(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+        }
+        if (lane == 0) {
+            sh.h = h;
+            sh.mv = mv;
+            sh.mn = mn;
+            sh.mb = mb;
+        }
+    }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
+{
+    DevState *st = p.st;
+    if (*(volatile int *)&st->done)
+        return;
+    __shared__ ReduceShared sh;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    reduce_stats(p.part_stat, p.G, sh);
+    __syncthreads();
+    const long long h = sh.h;
+    const double mv = sh.mv, mn = sh.mn, mb = sh.mb;
+    const int stop = st->stop;
+    const double eps = st->eps;
+    const bool force = st->force_step != 0;
+    const bool pass = !force && ((stop != NSLI_STOP_NONE && h == 0) || (stop == NSLI_STOP_EPSMEM && mn < eps) ||
+                                 (stop == NSLI_STOP_MAXVIOL_REL && mv <= eps * mb));
+    const bool at_max = !pass && (st->it >= st->max_iter);
+    const bool step = !pass && !at_max;
+    const int rule = st->rule;
+    const double lambda = st->lambda;
+    const long long j = (long long)blockIdx.x * kReduceCols + lane;
+
+    if (step) {
+        double yj = 0.0;
+        if (j < p.ld) {
+            const Acc *py = static_cast<const Acc *>(p.part_y);
+            for (int g = grp; g < p.G; g += 8)
+                yj += (double)py[(long long)g * p.ld + j];
+        }
+        sh.part[grp][lane] = yj;
+    }
+    __syncthreads();
+    if (step && grp == 0) {
+        double y = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            y += sh.part[q][lane];
+        double val = 0.0;
+        if (j < p.ld) {
+            if (rule == NSLI_RULE_MODAP) {
+                p.ybuf[j] = y;
+                val = y * y;
+            } else {
+                const double s = h > 0 ? lambda / (double)h : 0.0;
+                Acc *x = static_cast<Acc *>(p.x);
+                const Acc xo = x[j];
+                const Acc xn = (Acc)((double)xo - s * y);
+                x[j] = xn;
+                const double d = (double)xn - (double)xo;
+                val = d * d;
+            }
+        }
+        val = warp_sum(val);
+        if (lane == 0)
+            p.part_dx[blockIdx.x] = val;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(&st->ticket, 1u);
+        sh.last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sh.last)
+        return;
+    __threadfence();
+
+    double dx2 = 0.0, ynorm = 0.0;
+    if (step) {
+        if (grp == 0) {
+            double v = 0.0;
+            for (int q = lane; q < (int)gridDim.x; q += 32)
+                v += __ldcg(p.part_dx + q);
+            v = warp_sum(v);
+            if (lane == 0)
+                sh.red[0] = v;
+        }
+        __syncthreads();
+        const double tot = sh.red[0];
+        if (rule == NSLI_RULE_MODAP) {
+            ynorm = sqrt(tot);
+            const double s = ynorm > 0.0 ? lambda / ynorm : 0.0;
+            Acc *x = static_cast<Acc *>(p.x);
+            double v = 0.0;
+            for (long long q = threadIdx.x; q < p.ld; q += blockDim.x) {
+                const Acc xo = x[q];
+                const Acc xn = (Acc)((double)xo - s * __ldcg(p.ybuf + q));
+                x[q] = xn;
+                const double d = (double)xn - (double)xo;
+                v += d * d;
+            }
+            v = warp_sum(v);
+            __syncthreads();
+            if (lane == 0)
+                sh.part[0][grp] = v;
+            __syncthreads();
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q)
+                t += sh.part[0][q];
+            dx2 = t;
+        } else {
+            dx2 = tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        st->h = h;
+        st->maxviol = mv;
+        st->maxnorm = mn;
+        st->maxb = mb;
+        if (pass) {
+            st->status = ST_CANDIDATE;
+            st->done = 1;
+        } else if (at_max) {
+            st->status = NSLI_NOT_CONVERGED;
+            st->done = 1;
+        } else {
+            st->it += 1;
+            st->tick += 1;
+            st->dx_norm = sqrt(dx2);
+            st->y_norm = ynorm;
+            if (stop == NSLI_STOP_STEP && sqrt(dx2) < eps) {
+                st->status = NSLI_OK;
+                st->done = 1;
+            }
+        }
+        st->force_step = 0;
+        st->ticket = 0u;
+    }
+}
+
+// Map + Reduce without a step (diagnostics and parity): y in binary64.
+template <typename Acc>
+__global__ void __launch_bounds__(256) reduce_only_kernel(const ReduceArgs p, double *y_out)
+{
+    __shared__ ReduceShared sh;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const long long j = (long long)blockIdx.x * kReduceCols + lane;
+    double yj = 0.0;
+    if (j < p.ld) {
+        const Acc *py = static_cast<const Acc *>(p.part_y);
+        for (int g = grp; g < p.G; g += 8)
+            yj += (double)py[(long long)g * p.ld + j];
+    }
+    sh.part[grp][lane] = yj;
+    __syncthreads();
+    if (grp == 0 && j < p.ld) {
+        double y = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            y += sh.part[q][lane];
+        y_out[j] = y;
+    }
+    if (blockIdx.x == 0) {
+        reduce_stats(p.part_stat, p.G, sh);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            p.st->h = sh.h;
+            p.st->maxviol = sh.mv;
+            p.st->maxnorm = sh.mn;
+            p.st->maxb = sh.mb;
+        }
+    }
+}
+
+// ------------------------------------------------------- binary64 check ----
+
+__device__ __forceinline__ unsigned long long ord_enc(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// One warp per row: r_i = sum_j a_ij x_j - (b0_i + (k rho) Av_i) with binary64
+// products and sums on the stored entries; maxima by order-preserving
+// integer atomics (exact, so the result does not depend on the schedule).
+template <int S>
+__global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs p)
+{
+    using Tr = Traits<S>;
+    using Acc = typename Tr::acc;
+    constexpr int EPV = Tr::EPV;
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double kr = __dmul_rn((double)p.st->tick, p.st->rho);
+    const Acc *x = static_cast<const Acc *>(p.x);
+    const long long row_bytes = (long long)p.nv * 16;
+    double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+    unsigned long long h = 0;
+    for (long long i = wg; i < p.m; i += nw) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(p.A) + i * row_bytes);
+        double s = 0.0;
+        for (int j = lane; j < p.nv; j += 32) {
+            Acc a[EPV];
+            decode<S>(__ldg(row + j), a);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e)
+                s = fma((double)a[e], (double)x[(long long)j * EPV + e], s);
+        }
+        s = warp_sum(s);
+        if (S == NSLI_FP8E4M3)
+            s = s * (double)p.scale[i];
+        const double bi = __dadd_rn(p.b0_64[i], __dmul_rn(kr, p.av_64[i]));
+        const double ri = s - bi;
+        mv = fmax(mv, ri);
+        mn = fmax(mn, ri / sqrt(p.n2_64[i]));
+        mb = fmax(mb, fabs(bi));
+        h += (ri > 0.0) ? 1ull : 0ull;
+    }
+    if (lane == 0) {
+        atomicMax(&p.out->maxviol, ord_enc(mv));
+        atomicMax(&p.out->maxnorm, ord_enc(mn));
+        atomicMax(&p.out->maxb, ord_enc(mb));
+        atomicAdd(&p.out->h, h);
+    }
+}
+
+// ---------------------------------------------------------------- set-up ----
+
+// One block per row: optional FP8 row scale, store the row in the storage
+// type (zero padding up to ld), binary64 ||a_i||^2 of the STORED values in a
+// fixed order, finiteness and zero-row flags.
+template <int S>
+__global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
+{
+    const long long r = blockIdx.x;
+    if (r >= p.rows)
+        return;
+    const long long gi = p.row0 + r;
+    __shared__ double sred[8];
+    __shared__ float samax[8];
+    __shared__ int sbad;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        sbad = 0;
+    __syncthreads();
+    const float *s32 = static_cast<const float *>(p.src) + r * p.lda;
+    const double *s64 = static_cast<const double *>(p.src) + r * p.lda;
+    int bad = 0;
+
+    float scale = 1.0f, inv_scale = 1.0f;
+    if (S == NSLI_FP8E4M3) {
+        float amax = 0.0f;
+        for (long long j = threadIdx.x; j < p.n; j += blockDim.x) {
+            const float a = s32[j];
+            if (!isfinite(a))
+                bad = 1;
+            amax = fmaxf(amax, fabsf(a));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        if (lane == 0)
+            samax[wid] = amax;
+        __syncthreads();
+        amax = 0.0f;
+        for (int q = 0; q < 8; ++q)
+            amax = fmaxf(amax, samax[q]);
+        int e = 0;
+        if (amax > 0.0f && isfinite(amax)) {
+            int e2;
+            const float f = frexpf(amax, &e2);  // amax = f 2^e2, f in [0.5, 1)
+            e = (f <= 0.875f) ? e2 - 9 : e2 - 8;  // smallest 2^e with amax / 2^e <= 448
+        }
+        scale = ldexpf(1.0f, e);
+        inv_scale = ldexpf(1.0f, -e);
+        if (threadIdx.x == 0)
+            p.scale[gi] = scale;
+    }
+
+    double n2 = 0.0;
+    for (long long j = threadIdx.x; j < p.ld; j += blockDim.x) {
+        const bool in = j < p.n;
+        if (S == NSLI_F64) {
+            const double v = in ? (p.src_f64 ? s64[j] : (double)s32[j]) : 0.0;
+            if (in && !isfinite(v))
+                bad = 1;
+            static_cast<double *>(p.A)[gi * p.ld + j] = v;
+            n2 += v * v;
+        } else if (S == NSLI_F32) {
+            const float v = in ? (p.src_f64 ? __double2float_rn(s64[j]) : s32[j]) : 0.0f;
+            if (in && !(p.src_f64 ? isfinite(s64[j]) : isfinite(v)))
+                bad = 1;
+            static_cast<float *>(p.A)[gi * p.ld + j] = v;
+            n2 += (double)v * (double)v;
+        } else if (S == NSLI_BF16) {
+            const float a = in ? s32[j] : 0.0f;
+            if (in && !isfinite(a))
+                bad = 1;
+            const __nv_bfloat16 q = __float2bfloat16_rn(a);
+            static_cast<__nv_bfloat16 *>(p.A)[gi * p.ld + j] = q;
+            const double v = (double)__bfloat162float(q);
+            n2 += v * v;
+        } else {
+            const float a = in ? s32[j] : 0.0f;
+            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
+            static_cast<unsigned char *>(p.A)[gi * p.ld + j] = (unsigned char)q;
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+            const double v = (double)__half2float(__half(hr)) * (double)scale;
+            n2 += v * v;
+        }
+    }
+    n2 = warp_sum(n2);
+    if (bad)
+        sbad = 1;
+    if (lane == 0)
+        sred[wid] = n2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+            t += sred[q];
+        if (p.norms_in != nullptr)
+            t = p.norms_in[gi];
+        p.n2_64[gi] = t;
+        int f = 0;
+        if (sbad || !isfinite(t))
+            f |= PREPF_NONFINITE;
+        if (t == 0.0)
+            f |= PREPF_ZERO_ROW;
+        if (f)
+            atomicOr(p.flags, f);
+    }
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(256) meta_kernel(const MetaArgs p)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.m)
+        return;
+    const double b0 = p.b0_64[i];
+    const double av = p.av_64[i];
+    const double n2 = p.n2_64[i];
+    if (!isfinite(b0) || !isfinite(av))
+        atomicOr(p.flags, PREPF_NONFINITE);
+    const double inv_n2 = 1.0 / n2;
+    const double inv_n = 1.0 / sqrt(n2);
+    if (F64) {
+        RowMeta64 m{b0, av, inv_n2, inv_n};
+        static_cast<RowMeta64 *>(p.meta)[i] = m;
+    } else {
+        RowMeta32 m{(float)b0, (float)av, (float)inv_n2, (float)inv_n,
+                    p.scale ? p.scale[i] : 1.0f, 0.0f, 0.0f, 0.0f};
+        static_cast<RowMeta32 *>(p.meta)[i] = m;
+    }
+}
+
+template <typename Acc>
+__global__ void x_from_f64_kernel(const double *src, Acc *x, long long n, long long ld, int *flags)
+{
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ld)
+        return;
+    double v = 0.0;
+    if (j < n) {
+        v = src[j];
+        if (!isfinite(v))
+            atomicOr(flags, PREPF_NONFINITE);
+    }
+    x[j] = (Acc)v;
+}
+
+template <typename Acc>
+__global__ void x_to_f64_kernel(const Acc *x, double *dst, long long n)
+{
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n)
+        dst[j] = (double)x[j];
+}
+
+__global__ void check_finite_kernel(const double *v, long long n, int *flags)
+{
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && !isfinite(v[j]))
+        atomicOr(flags, PREPF_NONFINITE);
+}
+
+__global__ void state_begin_kernel(DevState *st, const StateBegin b)
+{
+    st->lambda = b.lambda;
+    st->eps = b.eps;
+    st->rho = b.rho;
+    st->max_iter = b.max_iter;
+    st->rule = b.rule;
+    st->stop = b.stop;
+    st->force_step = b.force_step;
+    if (b.reset_it)
+        st->it = 0;
+    if (b.tick >= 0)
+        st->tick = b.tick;
+    st->done = 0;
+    st->status = ST_RUNNING;
+    st->error = 0;
+    st->ticket = 0u;
+}
+
+__global__ void state_resume_kernel(DevState *st)
+{
+    st->done = 0;
+    st->status = ST_RUNNING;
+    st->force_step = 1;
+}
+
+// Exact values of stored rows as binary64 (diagnostics).
+template <int S>
+__global__ void stored_rows_kernel(const void *A, const float *scale, long long ld, long long n, long long row0,
+                                   long long rows, double *out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * n)
+        return;
+    const long long r = t / n, j = t % n;
+    const long long i = row0 + r;
+    double v;
+    if (S == NSLI_F64) {
+        v = static_cast<const double *>(A)[i * ld + j];
+    } else if (S == NSLI_F32) {
+        v = (double)static_cast<const float *>(A)[i * ld + j];
+    } else if (S == NSLI_BF16) {
+        v = (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(A)[i * ld + j]);
+    } else {
+        const __nv_fp8_storage_t q = static_cast<const unsigned char *>(A)[i * ld + j];
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        v = (double)__half2float(__half(hr)) * (double)scale[i];
+    }
+    out[t] = v;
+}
+
+// ------------------------------------------------------------- launchers ----
+
+int map_vpt_limit(int storage)
+{
+    switch (storage) {
+    case NSLI_F64: return 8;
+    case NSLI_F32: return 8;
+    case NSLI_BF16: return 4;
+    case NSLI_FP8E4M3: return 2;
+    default: return 0;
+    }
+}
+
+template <int S> static const void *map_fn(int vpt)
+{
+    switch (vpt) {
+    case 1: return (const void *)map_kernel<S, 1>;
+    case 2: return (const void *)map_kernel<S, 2>;
+    case 4:
+        if constexpr (S != NSLI_FP8E4M3)
+            return (const void *)map_kernel<S, 4>;
+        return nullptr;
+    case 8:
+        if constexpr (S == NSLI_F64 || S == NSLI_F32)
+            return (const void *)map_kernel<S, 8>;
+        return nullptr;
+    default: return nullptr;
+    }
+}
+
+static const void *map_fn_any(int storage, int vpt)
+{
+    switch (storage) {
+    case NSLI_F64: return map_fn<NSLI_F64>(vpt);
+    case NSLI_F32: return map_fn<NSLI_F32>(vpt);
+    case NSLI_BF16: return map_fn<NSLI_BF16>(vpt);
+    case NSLI_FP8E4M3: return map_fn<NSLI_FP8E4M3>(vpt);
+    default: return nullptr;
+    }
+}
+
+cudaError_t map_prepare(int storage, int vpt, size_t smem)
+{
+    const void *fn = map_fn_any(storage, vpt);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t map_launch(int storage, int vpt, int grid, int consumers, size_t smem, cudaStream_t s,
+                       const MapArgs &a)
+{
+    const void *fn = map_fn_any(storage, vpt);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    void *args[] = {const_cast<MapArgs *>(&a)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(consumers), args, smem, s);
+}
+
+cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a)
+{
+    if (f64)
+        reduce_update_kernel<double><<<grid, 256, 0, s>>>(a);
+    else
+        reduce_update_kernel<float><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a, double *y_out)
+{
+    if (f64)
+        reduce_only_kernel<double><<<grid, 256, 0, s>>>(a, y_out);
+    else
+        reduce_only_kernel<float><<<grid, 256, 0, s>>>(a, y_out);
+    return cudaGetLastError();
+}
+
+cudaError_t verify_launch(int storage, int grid, cudaStream_t s, const VerifyArgs &a)
+{
+    switch (storage) {
+    case NSLI_F64: verify_kernel<NSLI_F64><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_F32: verify_kernel<NSLI_F32><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_BF16: verify_kernel<NSLI_BF16><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_FP8E4M3: verify_kernel<NSLI_FP8E4M3><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a)
+{
+    const unsigned int grid = (unsigned int)a.rows;
+    switch (storage) {
+    case NSLI_F64: prep_kernel<NSLI_F64><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_F32: prep_kernel<NSLI_F32><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_BF16: prep_kernel<NSLI_BF16><<<grid, 256, 0, s>>>(a); break;
+    case NSLI_FP8E4M3: prep_kernel<NSLI_FP8E4M3><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a)
+{
+    const unsigned int grid = (unsigned int)((a.m + 255) / 256);
+    if (f64)
+        meta_kernel<true><<<grid, 256, 0, s>>>(a);
+    else
+        meta_kernel<false><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, void *x, long long n, long long ld,
+                              int *flags)
+{
+    const unsigned int grid = (unsigned int)((ld + 255) / 256);
+    if (f64)
+        x_from_f64_kernel<double><<<grid, 256, 0, s>>>(src, static_cast<double *>(x), n, ld, flags);
+    else
+        x_from_f64_kernel<float><<<grid, 256, 0, s>>>(src, static_cast<float *>(x), n, ld, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t x_to_f64_launch(bool f64, cudaStream_t s, const void *x, double *dst, long long n)
+{
+    const unsigned int grid = (unsigned int)((n + 255) / 256);
+    if (f64)
+        x_to_f64_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(x), dst, n);
+    else
+        x_to_f64_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(x), dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite_launch(cudaStream_t s, const double *v, long long n, int *flags)
+{
+    const unsigned int grid = (unsigned int)((n + 255) / 256);
+    check_finite_kernel<<<grid, 256, 0, s>>>(v, n, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b)
+{
+    state_begin_kernel<<<1, 1, 0, s>>>(st, b);
+    return cudaGetLastError();
+}
+
+cudaError_t state_resume_launch(cudaStream_t s, DevState *st)
+{
+    state_resume_kernel<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
+                               long long n, long long row0, long long rows, double *out)
+{
+    const long long total = rows * n;
+    const unsigned int grid = (unsigned int)((total + 255) / 256);
+    switch (storage) {
+    case NSLI_F64: stored_rows_kernel<NSLI_F64><<<grid, 256, 0, s>>>(A, scale, ld, n, row0, rows, out); break;
+    case NSLI_F32: stored_rows_kernel<NSLI_F32><<<grid, 256, 0, s>>>(A, scale, ld, n, row0, rows, out); break;
+    case NSLI_BF16: stored_rows_kernel<NSLI_BF16><<<grid, 256, 0, s>>>(A, scale, ld, n, row0, rows, out); break;
+    case NSLI_FP8E4M3:
+        stored_rows_kernel<NSLI_FP8E4M3><<<grid, 256, 0, s>>>(A, scale, ld, n, row0, rows, out);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nsli

@@ -1,0 +1,321 @@
+"""Python binding of the C ABI in ``include/nsli.h`` (argument marshalling only).
+
+Every step of the method runs in ``libnsli.so`` (CUDA, sm_103a).  The binding
+never computes any part of the method; when the library is missing it raises
+instead of falling back to anything else.
+
+Functions carry the C names (``nsli_create``, ``nsli_update_b``,
+``nsli_iterate``, ``nsli_solve``, ``nsli_residual_max``, ...).  ``Solver``
+wraps a handle for numpy arrays (host memory) or CUDA torch tensors (device
+memory); the library detects which from the pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
+RULE_RELAXED, RULE_MODAP = 0, 1
+STOP_NONE, STOP_STEP, STOP_EPSMEM, STOP_MAXVIOL_REL = 0, 1, 2, 3
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_ZERO_ROW, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7)
+
+STORAGE = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8E4M3, "e4m3": FP8E4M3}
+RULES = {"relaxed": RULE_RELAXED, "modap": RULE_MODAP}
+STOPS = {"none": STOP_NONE, "step": STOP_STEP, "epsmem": STOP_EPSMEM,
+         "maxviol_rel": STOP_MAXVIOL_REL}
+
+
+class nsli_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("rule", ctypes.c_int32),
+                ("stop", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("max_iter", ctypes.c_int64), ("block_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rho", ctypes.c_double)]
+
+
+class nsli_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("tick", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("h", ctypes.c_int64), ("max_viol", ctypes.c_double),
+                ("max_viol_norm", ctypes.c_double), ("max_abs_b", ctypes.c_double),
+                ("last_step_norm", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class NsliError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (where, strerror(code), code)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+_lib = None
+_lock = threading.Lock()
+EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
+           "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
+           "nsli_get_stored_rows", "nsli_get_norms2",
+           "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
+           "nsli_strerror", "nsli_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libnsli.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                "libnsli.so is not built (%s); run `python -c \"import __graft_entry__ as g; "
+                "g.build()\"` first -- there is no fallback" % p)
+        lib = ctypes.CDLL(p)
+        P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        H = ctypes.c_void_p
+        lib.nsli_create.argtypes = [ctypes.POINTER(H), i64, i64, i32, i32, P, i64, P, P, P, P, P]
+        lib.nsli_create.restype = ctypes.c_int
+        lib.nsli_update_b.argtypes = [H, P, i64]
+        lib.nsli_update_b.restype = ctypes.c_int
+        lib.nsli_iterate.argtypes = [H, ctypes.POINTER(nsli_params), i64]
+        lib.nsli_iterate.restype = ctypes.c_int
+        lib.nsli_iterate_timed.argtypes = [H, ctypes.POINTER(nsli_params), i64, P]
+        lib.nsli_iterate_timed.restype = ctypes.c_int
+        lib.nsli_solve.argtypes = [H, ctypes.POINTER(nsli_params), ctypes.POINTER(nsli_result)]
+        lib.nsli_solve.restype = ctypes.c_int
+        lib.nsli_residual_max.argtypes = [H, ctypes.POINTER(d), ctypes.POINTER(d)]
+        lib.nsli_residual_max.restype = ctypes.c_int
+        lib.nsli_map_reduce.argtypes = [H, P, ctypes.POINTER(i64), P]
+        lib.nsli_map_reduce.restype = ctypes.c_int
+        lib.nsli_get_x.argtypes = [H, P]
+        lib.nsli_get_x.restype = ctypes.c_int
+        lib.nsli_set_x.argtypes = [H, P]
+        lib.nsli_set_x.restype = ctypes.c_int
+        lib.nsli_get_stored_rows.argtypes = [H, i64, i64, P]
+        lib.nsli_get_stored_rows.restype = ctypes.c_int
+        lib.nsli_get_norms2.argtypes = [H, P]
+        lib.nsli_get_norms2.restype = ctypes.c_int
+        lib.nsli_get_result.argtypes = [H, ctypes.POINTER(nsli_result)]
+        lib.nsli_get_result.restype = ctypes.c_int
+        lib.nsli_launch_count.argtypes = [H]
+        lib.nsli_launch_count.restype = i64
+        lib.nsli_sync.argtypes = [H]
+        lib.nsli_sync.restype = ctypes.c_int
+        lib.nsli_destroy.argtypes = [H]
+        lib.nsli_destroy.restype = None
+        lib.nsli_strerror.argtypes = [ctypes.c_int]
+        lib.nsli_strerror.restype = ctypes.c_char_p
+        lib.nsli_last_error.argtypes = [H]
+        lib.nsli_last_error.restype = ctypes.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().nsli_strerror(int(code)).decode()
+    except Exception:
+        return "status %d" % code
+
+
+def _ptr(a):
+    """Address of a numpy array (host) or a CUDA tensor (device); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    else:
+        import torch
+        a = a.to(torch.float64).contiguous()
+    if n is not None and a.shape[0] != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.shape[0]))
+    return a
+
+
+def _check(code: int, where: str, h=None) -> int:
+    if code < 0:
+        detail = ""
+        if h is not None:
+            detail = load().nsli_last_error(h).decode()
+        raise NsliError(code, where, detail)
+    return code
+
+
+def _sync_torch_inputs(*arrays):
+    for a in arrays:
+        if a is not None and hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
+            return
+
+
+def make_params(lam=1.0, rule="relaxed", stop="none", eps=0.0, max_iter=0,
+                block_iters=0, rho=0.0) -> nsli_params:
+    p = nsli_params()
+    p.lambda_ = float(lam)
+    p.rule = RULES[rule] if isinstance(rule, str) else int(rule)
+    p.stop = STOPS[stop] if isinstance(stop, str) else int(stop)
+    p.eps = float(eps)
+    p.max_iter = int(max_iter)
+    p.block_iters = int(block_iters)
+    p.reserved = 0
+    p.rho = float(rho)
+    return p
+
+
+class Solver:
+    """One problem resident on the current CUDA device.
+
+    A: (m, n) float32 or float64 array/tensor (row-major); b0, Av, norms2:
+    length-m float64; x0: length-n float64.  ``storage`` is "f64", "f32",
+    "bf16" or "fp8"."""
+
+    def __init__(self, A, b0, x0, Av=None, norms2=None, storage="f32", stream=None):
+        lib = load()
+        m, n = int(A.shape[0]), int(A.shape[1])
+        if isinstance(A, np.ndarray):
+            if A.dtype not in (np.float32, np.float64):
+                A = A.astype(np.float32)
+            A = np.ascontiguousarray(A)
+            a_dtype = F64 if A.dtype == np.float64 else F32
+        else:
+            import torch
+            if A.dtype not in (torch.float32, torch.float64):
+                A = A.to(torch.float32)
+            A = A.contiguous()
+            a_dtype = F64 if A.dtype == torch.float64 else F32
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        b0, x0, Av, norms2 = _f64(b0, m), _f64(x0, n), _f64(Av, m), _f64(norms2, m)
+        _sync_torch_inputs(A, b0, x0, Av, norms2)
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream)
+        rc = lib.nsli_create(ctypes.byref(h), m, n, self.storage, a_dtype, _ptr(A), n,
+                             _ptr(b0), _ptr(norms2), _ptr(Av), _ptr(x0), s)
+        if rc != OK:
+            raise NsliError(rc, "nsli_create")
+        self._h = h
+        self.m, self.n = m, n
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nsli_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- calls
+    def update_b(self, b0=None, tick=-1):
+        b0 = _f64(b0, self.m)
+        _sync_torch_inputs(b0)
+        _check(load().nsli_update_b(self._h, _ptr(b0), int(tick)), "nsli_update_b", self._h)
+
+    def iterate(self, n_iter, lam=1.0, rule="relaxed", rho=0.0, block_iters=0):
+        p = make_params(lam=lam, rule=rule, rho=rho, block_iters=block_iters)
+        _check(load().nsli_iterate(self._h, ctypes.byref(p), int(n_iter)), "nsli_iterate", self._h)
+
+    def iterate_timed(self, n_iter, lam=1.0, rule="relaxed", rho=0.0):
+        """Run n_iter iterations kernel by kernel; return summed device ms of
+        (Map kernels, Reduce-and-step kernels)."""
+        p = make_params(lam=lam, rule=rule, rho=rho)
+        ms = np.zeros(2, np.float64)
+        _check(load().nsli_iterate_timed(self._h, ctypes.byref(p), int(n_iter), _ptr(ms)),
+               "nsli_iterate_timed", self._h)
+        return float(ms[0]), float(ms[1])
+
+    def solve(self, lam=1.0, rule="relaxed", stop="step", eps=1e-8, max_iter=100000,
+              rho=0.0, block_iters=0) -> dict:
+        p = make_params(lam=lam, rule=rule, stop=stop, eps=eps, max_iter=max_iter,
+                        rho=rho, block_iters=block_iters)
+        r = nsli_result()
+        _check(load().nsli_solve(self._h, ctypes.byref(p), ctypes.byref(r)), "nsli_solve", self._h)
+        return r.as_dict()
+
+    def residual_max(self) -> tuple[float, float]:
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().nsli_residual_max(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "nsli_residual_max", self._h)
+        return a.value, b.value
+
+    def map_reduce(self):
+        y = np.empty(self.n, np.float64)
+        hv = ctypes.c_int64()
+        stats = np.empty(3, np.float64)
+        _check(load().nsli_map_reduce(self._h, _ptr(y), ctypes.byref(hv), _ptr(stats)),
+               "nsli_map_reduce", self._h)
+        return y, int(hv.value), {"maxviol": stats[0], "maxnorm": stats[1], "maxb": stats[2]}
+
+    def get_x(self, out=None):
+        x = np.empty(self.n, np.float64) if out is None else out
+        _check(load().nsli_get_x(self._h, _ptr(x)), "nsli_get_x", self._h)
+        return x
+
+    def set_x(self, x):
+        x = _f64(x, self.n)
+        _sync_torch_inputs(x)
+        _check(load().nsli_set_x(self._h, _ptr(x)), "nsli_set_x", self._h)
+
+    def stored_rows(self, row0=0, rows=None):
+        rows = self.m - row0 if rows is None else rows
+        out = np.empty((rows, self.n), np.float64)
+        _check(load().nsli_get_stored_rows(self._h, int(row0), int(rows), _ptr(out)),
+               "nsli_get_stored_rows", self._h)
+        return out
+
+    def norms2(self):
+        out = np.empty(self.m, np.float64)
+        _check(load().nsli_get_norms2(self._h, _ptr(out)), "nsli_get_norms2", self._h)
+        return out
+
+    def result(self) -> dict:
+        r = nsli_result()
+        _check(load().nsli_get_result(self._h, ctypes.byref(r)), "nsli_get_result", self._h)
+        return r.as_dict()
+
+    def launch_count(self) -> int:
+        return int(load().nsli_launch_count(self._h))
+
+    def sync(self):
+        _check(load().nsli_sync(self._h), "nsli_sync", self._h)

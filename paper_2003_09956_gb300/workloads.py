@@ -44,19 +44,29 @@ def _threads() -> int:
     return max(1, min(32, os.cpu_count() or 1))
 
 
-def gaussian_matrix(m: int, n: int, seed: int) -> np.ndarray:
-    """m x n float32 matrix with N(0, 1) entries, drawn in row chunks."""
-    A = np.empty((m, n), np.float32)
+def gaussian_matrix(m: int, n: int, seed: int, rows: tuple[int, int] | None = None) -> np.ndarray:
+    """m x n float32 matrix with N(0, 1) entries, drawn in row chunks.
+
+    ``rows=(r0, r1)`` returns only rows r0..r1-1 of that same matrix (r0 a
+    multiple of the chunk size), without drawing the others."""
+    r_lo, r_hi = (0, m) if rows is None else rows
+    if r_lo % _CHUNK_ROWS:
+        raise ValueError("row window must start on a chunk boundary")
+    A = np.empty((r_hi - r_lo, n), np.float32)
     seqs, _ = _chunk_rngs(seed, m)
 
     def fill(c):
         r0 = c * _CHUNK_ROWS
-        r1 = min(m, r0 + _CHUNK_ROWS)
+        r1 = min(r_hi, r0 + _CHUNK_ROWS)
         g = np.random.Generator(np.random.PCG64(seqs[c]))
-        g.standard_normal((r1 - r0, n), dtype=np.float32, out=A[r0:r1])
+        if r1 - r0 == _CHUNK_ROWS or r1 == min(m, r0 + _CHUNK_ROWS):
+            g.standard_normal((r1 - r0, n), dtype=np.float32, out=A[r0 - r_lo:r1 - r_lo])
+        else:
+            A[r0 - r_lo:r1 - r_lo] = g.standard_normal((min(m, r0 + _CHUNK_ROWS) - r0, n),
+                                                       dtype=np.float32)[:r1 - r0]
 
     with _cf.ThreadPoolExecutor(_threads()) as ex:
-        list(ex.map(fill, range(len(seqs))))
+        list(ex.map(fill, range(r_lo // _CHUNK_ROWS, (r_hi + _CHUNK_ROWS - 1) // _CHUNK_ROWS)))
     return A
 
 
@@ -102,15 +112,20 @@ def _matvec_f64(A: np.ndarray, v: np.ndarray) -> np.ndarray:
 
 
 def dense_system(m: int, n: int, seed: int, grid: str | None = None,
-                 x0_std: float = 5.0) -> dict:
-    """The non-stationary dense random system (see the module docstring)."""
-    A = round_to_grid(gaussian_matrix(m, n, seed), grid)
+                 x0_std: float = 5.0, rows: tuple[int, int] | None = None) -> dict:
+    """The non-stationary dense random system (see the module docstring).
+
+    ``rows=(r0, r1)`` gives the same system restricted to rows r0..r1-1
+    (A, b0, Av sliced; z, v, x0 unchanged)."""
+    A = round_to_grid(gaussian_matrix(m, n, seed, rows=rows), grid)
     _, g = _chunk_rngs(seed, m)
     z = g.uniform(-1.0, 1.0, n)
     slack = g.uniform(0.1, 1.0, m)
     dirn = g.standard_normal(n)
     v = dirn / np.sqrt(np.sum(dirn * dirn))
     x0 = g.normal(0.0, x0_std, n).astype(np.float32).astype(np.float64)
+    if rows is not None:
+        slack = slack[rows[0]:rows[1]]
     b0 = _matvec_f64(A, z) + slack
     Av = _matvec_f64(A, v)
     return {"A": A, "b0": b0, "Av": Av, "x0": x0, "z": z, "v": v,

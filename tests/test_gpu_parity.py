@@ -1,0 +1,352 @@
+"""CUDA path against the FP64 oracle, through the C ABI, on seeded inputs.
+
+Floating point decides an integer in the Map (row violated or not).  Rows
+whose oracle residual lies within a rigorous bound of the accumulation
+type's rounding error are "ambiguous": either classification is correct,
+so the checks accept both and bound their (tiny) contribution; everything
+else is compared element by element.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_09956_gb300 import nsli, workloads
+
+pytestmark = pytest.mark.gpu
+
+U = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24, "fp8": 2.0 ** -24}
+STORAGES = ["f64", "f32", "bf16", "fp8"]
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    from paper_2003_09956_gb300 import _build
+    _build.build()
+    nsli.load()
+
+
+def stored_values(A32, storage):
+    """Exact values the stored matrix holds, from the oracle's quantizers."""
+    if storage == "bf16":
+        return oracle.quantize_bf16(A32)
+    if storage == "fp8":
+        q, _ = oracle.quantize_e4m3_rows(A32)
+        return q
+    return A32
+
+
+def ambiguity_bound(A, x, b, u):
+    """|computed r_i - exact r_i| <= bound_i for the kernel's accumulation
+    (per-thread sequential partial sums of at most 32 products, a 5-level
+    warp tree and a <= 16-term block sum): gamma_k * (sum |a_ij x_j| + |b_i|)
+    with k = 64 levels and a factor 4 of slack."""
+    Ad = np.asarray(A, np.float64)
+    return 4.0 * 64 * u * (np.abs(Ad) @ np.abs(x) + np.abs(b) + 1e-300)
+
+
+def check_map_reduce(solver, A_eff, b, x, storage, tol_rel=1e-5):
+    y_g, h_g, st_g = solver.map_reduce()
+    n2, _ = oracle.norms2(A_eff)
+    mr = oracle.map_reduce(A_eff, b, n2, x)
+    r = mr["r"]
+    bound = ambiguity_bound(A_eff, x, b, U[storage])
+    amb = np.abs(r) <= bound
+    sure = (r > 0) & ~amb
+    h_sure = int(sure.sum())
+    assert h_sure <= h_g <= h_sure + int(amb.sum()), (h_g, h_sure, int(amb.sum()))
+    # oracle sum over the rows whose classification is fixed
+    keep = ~amb
+    if keep.all():
+        y_ref = mr["y"]
+    else:
+        y_ref = oracle.map_reduce(np.ascontiguousarray(A_eff[keep]), b[keep], n2[keep], x)["y"]
+    slack = float(np.sum(bound[amb] / np.sqrt(n2[amb]))) if amb.any() else 0.0
+    # each violated row's slice carries a rounding error bounded like its residual
+    slack += float(np.sum(bound[sure] / np.sqrt(n2[sure])))
+    err = np.linalg.norm(y_g - y_ref)
+    scale = np.linalg.norm(y_ref)
+    assert err <= tol_rel * scale + slack, (err, scale, slack)
+    # maxima (the kernel works in its accumulation type)
+    tol_m = 4 * float(bound.max()) + 1e-12
+    assert abs(st_g["maxviol"] - mr["maxviol"]) <= tol_m
+    assert abs(st_g["maxb"] - mr["maxb"]) <= 1e-6 * max(1.0, mr["maxb"])
+    return mr, h_g
+
+
+# ------------------------------------------------------------------ Map/Reduce
+
+SHAPES = [(1, 1), (7, 5), (300, 1), (150, 3), (1000, 333), (3001, 1000), (2000, 4100),
+          (600, 8192), (400, 16384)]
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_map_reduce_one_step(storage, m, n):
+    if storage == "f64" and n > 8192:
+        pytest.skip("binary64 rows are limited to n <= 8192")
+    p = workloads.dense_system(m, n, seed=1000 + m + n)
+    A_eff = stored_values(p["A"], storage)
+    src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+    with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        if storage in ("bf16", "fp8"):
+            np.testing.assert_array_equal(s.stored_rows(), A_eff.astype(np.float64))
+        n2, _ = oracle.norms2(A_eff)
+        np.testing.assert_allclose(s.norms2(), n2, rtol=1e-13)
+        check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_map_reduce_after_tick_and_new_b(storage):
+    m, n = 2500, 700
+    p = workloads.dense_system(m, n, seed=77)
+    A_eff = stored_values(p["A"], storage)
+    src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+    rng = np.random.default_rng(3)
+    b_new = p["b0"] + rng.uniform(-5, 5, m)
+    rho, tick = 0.25, 7
+    with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        s.iterate(0, rho=rho)          # sets rho on the device
+        s.update_b(b_new, tick=tick)
+        b_k = oracle.tick_b(b_new, p["Av"], rho, tick)
+        check_map_reduce(s, A_eff, b_k, p["x0"], storage)
+
+
+# ------------------------------------------------------------------ trajectories
+
+def oracle_trajectory(A_eff, p, rule, lam, rho, K, storage):
+    """x_1..x_K of the oracle, and the first iteration whose Map had an
+    ambiguous row (comparison is only meaningful before it)."""
+    n2, _ = oracle.norms2(A_eff)
+    xs, first_amb = [], K
+    x = p["x0"].copy()
+    for k in range(K):
+        code, x, st, y, r = oracle.iteration(A_eff, p["b0"], p["Av"], rho, k, n2, x,
+                                             lam=lam, rule=rule)
+        b_k = oracle.tick_b(p["b0"], p["Av"], rho, k)
+        bound = ambiguity_bound(A_eff, xs[-1] if xs else p["x0"], b_k, U[storage]) * 100
+        if first_amb == K and np.any(np.abs(r) <= bound):
+            first_amb = k
+        xs.append(x.copy())
+    return xs, first_amb
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("rule", ["relaxed", "modap"])
+@pytest.mark.parametrize("rho", [0.0, 1e-3])
+def test_trajectory_matches_oracle(storage, rule, rho):
+    m, n, K = 1500, 257, 15
+    p = workloads.dense_system(m, n, seed=5 + int(rho * 1e4))
+    A_eff = stored_values(p["A"], storage)
+    src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+    lam = 1.0 if rule == "relaxed" else 0.5
+    orule = oracle.RULE_RELAXED if rule == "relaxed" else oracle.RULE_MODAP
+    xs, first_amb = oracle_trajectory(A_eff, p, orule, lam, rho, K, storage)
+    assert first_amb >= 3, "seeded case became ambiguous too early"
+    tol = 1e-5 if storage != "f64" else 1e-12
+    with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        for k in range(first_amb):
+            s.iterate(1, lam=lam, rule=rule, rho=rho)
+            xg = s.get_x()
+            rel = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+            assert rel <= tol, (k, rel)
+        res = s.result()
+        assert res["iters"] == 1  # each iterate() call is one run of one update
+        assert res["tick"] == first_amb
+
+
+def test_graph_blocks_equal_single_launches():
+    """Iterations replayed from a captured graph equal direct launches, bit for bit."""
+    p = workloads.dense_system(3000, 515, seed=9)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"]) as s1, \
+            nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"]) as s2:
+        s1.iterate(40, rho=1e-3, block_iters=8)   # 5 graph replays
+        for _ in range(40):
+            s2.iterate(1, rho=1e-3)               # direct launches
+        np.testing.assert_array_equal(s1.get_x(), s2.get_x())
+        assert s1.result()["tick"] == s2.result()["tick"] == 40
+
+
+def test_deterministic_runs():
+    p = workloads.dense_system(4000, 1000, seed=10)
+    xs = []
+    for _ in range(3):
+        with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"]) as s:
+            s.iterate(25, rho=1e-4)
+            xs.append(s.get_x())
+    np.testing.assert_array_equal(xs[0], xs[1])
+    np.testing.assert_array_equal(xs[0], xs[2])
+
+
+def test_launch_count_two_kernels_per_iteration():
+    p = workloads.dense_system(500, 100, seed=11)
+    with nsli.Solver(p["A"], p["b0"], p["x0"]) as s:
+        c0 = s.launch_count()
+        s.iterate(64, block_iters=32)
+        s.sync()
+        assert s.launch_count() - c0 == 1 + 2 * 64   # state set-up + 2 per iteration
+
+
+# ------------------------------------------------------------------ solves
+
+@pytest.mark.parametrize("rule,lam", [("relaxed", 1.0), ("modap", 1.0)])
+def test_model_system_solve_f64(rule, lam):
+    """n = 256, m = 513 cube-with-cut-corner system, binary64, ||dx|| < 1e-8."""
+    p = workloads.model_system(256, seed=0)
+    orule = oracle.RULE_RELAXED if rule == "relaxed" else oracle.RULE_MODAP
+    ref = oracle.solve(p["A"], p["b0"], p["x0"], rule=orule, lam=lam,
+                       stop=oracle.STOP_STEP, eps=1e-8, max_iter=200000)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], storage="f64") as s:
+        res = s.solve(lam=lam, rule=rule, stop="step", eps=1e-8, max_iter=200000)
+        xg = s.get_x()
+    assert res["status"] == ref["status"] == nsli.OK
+    assert abs(res["iters"] - ref["iters"]) <= max(1, 0.01 * ref["iters"])
+    maxb = np.abs(p["b0"]).max()
+    assert res["max_viol"] <= 1e-6 * maxb
+    assert np.max(p["A"] @ xg - p["b0"]) <= 1e-6 * maxb
+    np.testing.assert_allclose(xg, ref["x"], rtol=0, atol=1e-6 * maxb)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_dense_solve_iteration_count_within_one_percent(storage):
+    """A small stationary dense system solved to max r_i <= 1e-6 max|b|."""
+    p = workloads.dense_system(256, 48, seed=21, grid=None if storage == "f32" else storage,
+                               x0_std=1.0)
+    A_eff = stored_values(p["A"], storage)
+    ref = oracle.solve(A_eff, p["b0"], p["x0"], stop=oracle.STOP_MAXVIOL_REL, eps=1e-6,
+                       max_iter=400000)
+    assert ref["status"] == oracle.OK
+    with nsli.Solver(p["A"], p["b0"], p["x0"], storage=storage) as s:
+        res = s.solve(stop="maxviol_rel", eps=1e-6, max_iter=400000, block_iters=64)
+    assert res["status"] == nsli.OK
+    assert abs(res["iters"] - ref["iters"]) <= max(2, 0.01 * ref["iters"]), (res["iters"], ref["iters"])
+    assert res["max_viol"] <= 1e-6 * res["max_abs_b"]
+
+
+def test_strictly_feasible_start_gpu():
+    p = workloads.dense_system(800, 64, seed=3)
+    for storage in STORAGES:
+        src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+        A_eff = stored_values(p["A"], storage)
+        z = p["z"].astype(np.float32).astype(np.float64)
+        if np.max(A_eff.astype(np.float64) @ z - p["b0"]) >= -1e-3:
+            continue
+        with nsli.Solver(src, p["b0"], z, storage=storage) as s:
+            res = s.solve(stop="step", eps=1e-8, max_iter=100)
+            assert res["status"] == nsli.OK and res["iters"] == 0 and res["h"] == 0
+            np.testing.assert_array_equal(s.get_x(), z)
+
+
+def test_modap_step_length_gpu():
+    p = workloads.dense_system(2000, 300, seed=4)
+    with nsli.Solver(p["A"], p["b0"], p["x0"]) as s:
+        for lam in (0.5, 2.0):
+            x0 = s.get_x()
+            s.iterate(1, lam=lam, rule="modap")
+            x1 = s.get_x()
+            assert np.linalg.norm(x1 - x0) == pytest.approx(lam, rel=1e-5)
+            assert s.result()["last_step_norm"] == pytest.approx(lam, rel=1e-5)
+
+
+def test_max_iter_and_not_converged():
+    p = workloads.model_system(64, seed=2)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], storage="f64") as s:
+        res = s.solve(stop="step", eps=1e-12, max_iter=5, block_iters=4)
+        assert res["status"] == nsli.NOT_CONVERGED and res["iters"] == 5
+        res = s.solve(stop="step", eps=1e-12, max_iter=0)
+        assert res["status"] == nsli.NOT_CONVERGED and res["iters"] == 0
+
+
+# ------------------------------------------------------------------ binary64 check
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_binary64_check_matches_oracle(storage):
+    m, n = 3000, 900
+    p = workloads.dense_system(m, n, seed=31)
+    A_eff = stored_values(p["A"], storage)
+    src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+    rng = np.random.default_rng(6)
+    x = rng.normal(0, 0.3, n).astype(np.float32).astype(np.float64)
+    rho, tick = 1e-2, 11
+    with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        s.set_x(x)
+        s.iterate(0, rho=rho)
+        s.update_b(None, tick=tick)
+        mv, mn = s.residual_max()
+    n2, _ = oracle.norms2(A_eff)
+    mr = oracle.map_reduce(A_eff, oracle.tick_b(p["b0"], p["Av"], rho, tick), n2, x)
+    assert mv == pytest.approx(mr["maxviol"], rel=1e-12, abs=1e-9)
+    assert mn == pytest.approx(mr["maxnorm"], rel=1e-12, abs=1e-9)
+
+
+# ------------------------------------------------------------------ errors
+
+def test_error_codes():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((20, 8)).astype(np.float32)
+    b = np.ones(20)
+    x = np.zeros(8)
+    bad = A.copy()
+    bad[3] = 0.0
+    with pytest.raises(nsli.NsliError) as e:
+        nsli.Solver(bad, b, x)
+    assert e.value.code == nsli.ERR_ZERO_ROW
+    bad = A.copy()
+    bad[2, 2] = np.nan
+    for storage in ("f32", "bf16", "fp8"):
+        with pytest.raises(nsli.NsliError) as e:
+            nsli.Solver(bad, b, x, storage=storage)
+        assert e.value.code == nsli.ERR_NONFINITE
+    bb = b.copy()
+    bb[0] = np.inf
+    with pytest.raises(nsli.NsliError) as e:
+        nsli.Solver(A, bb, x)
+    assert e.value.code == nsli.ERR_NONFINITE
+    xx = x.copy()
+    xx[1] = np.nan
+    with pytest.raises(nsli.NsliError) as e:
+        nsli.Solver(A, b, xx)
+    assert e.value.code == nsli.ERR_NONFINITE
+    with pytest.raises(nsli.NsliError) as e:
+        nsli.Solver(np.ones((2, 16385), np.float32), np.ones(2), np.zeros(16385))
+    assert e.value.code == nsli.ERR_UNSUPPORTED
+    with pytest.raises(nsli.NsliError) as e:
+        nsli.Solver(np.ones((2, 4), np.float64), np.ones(2), np.zeros(4), storage="bf16")
+    assert e.value.code == nsli.ERR_ARG
+    with nsli.Solver(A, b, x) as s:
+        with pytest.raises(nsli.NsliError) as e:
+            s.iterate(1, lam=-1.0)
+        assert e.value.code == nsli.ERR_ARG
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_b(np.full(20, np.nan))
+        assert e.value.code == nsli.ERR_NONFINITE
+
+
+# ------------------------------------------------------------------ full sizes
+
+@pytest.fixture(scope="module")
+def cfg2_system():
+    return workloads.dense_system(32768, 8192, seed=2004)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
+def test_full_size_32768x8192_one_step(cfg2_system, storage):
+    p = cfg2_system
+    A_eff = stored_values(p["A"], storage)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        s.iterate(0, rho=1e-4)
+        check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
+
+
+def test_full_size_131072x16384_f32_one_step_and_fejer():
+    """The benchmark's workload and launch shape: one Map/Reduce against the
+    oracle, then 6 stationary iterations whose distance to the interior point
+    z must not grow (Fejer property, any size)."""
+    p = workloads.dense_system(131072, 16384, seed=2005)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage="f32") as s:
+        check_map_reduce(s, p["A"], p["b0"], p["x0"], "f32")
+        d_prev = np.linalg.norm(s.get_x() - p["z"])
+        for _ in range(6):
+            s.iterate(1, rho=0.0)
+            d = np.linalg.norm(s.get_x() - p["z"])
+            assert d <= d_prev * (1 + 1e-6)
+            d_prev = d

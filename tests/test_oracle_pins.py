@@ -364,3 +364,19 @@ def test_e4m3_rounding_matches_library_bit_exact():
         assert s[0] == 1.0
         lib = torch.from_numpy(row).to(torch.float8_e4m3fn).to(torch.float32).numpy()
         np.testing.assert_array_equal(q, lib)
+
+
+def test_binary32_entry_points_match_double_entry_points():
+    """The binary32-input Map/Reduce and norms read the same exact values."""
+    rng = np.random.default_rng(4)
+    A32 = rng.standard_normal((60, 45)).astype(np.float32)
+    b = rng.standard_normal(60)
+    x = rng.standard_normal(45) * 3
+    n2a, _ = oracle.norms2(A32)
+    n2b, _ = oracle.norms2(A32.astype(np.float64))
+    np.testing.assert_array_equal(n2a, n2b)
+    m1 = oracle.map_reduce(A32, b, n2a, x)
+    m2 = oracle.map_reduce(A32.astype(np.float64), b, n2b, x)
+    np.testing.assert_array_equal(m1["y"], m2["y"])
+    np.testing.assert_array_equal(m1["r"], m2["r"])
+    assert m1["h"] == m2["h"]
