@@ -114,8 +114,9 @@ typedef struct {
  *             in binary64 on the device from the stored entries.
  *   Av        host or device, m doubles (A v for the translation direction
  *             v), or NULL for a stationary right-hand side.
- *   x0        host or device, n doubles: the starting point (rounded to the
- *             accumulation type: binary32 unless storage is NSLI_F64).
+ *   x0        host or device, n doubles: the starting point.  The iterate is
+ *             kept and updated in binary64; the Map reads its rounding to the
+ *             accumulation type (binary32 unless storage is NSLI_F64).
  *   stream    a cudaStream_t on the current device (not the legacy default
  *             stream: iteration blocks are captured into CUDA graphs), or
  *             NULL to let the handle create and own a non-blocking stream.

@@ -30,7 +30,7 @@ struct nsli_solver {
 
     void *A = nullptr, *meta = nullptr, *x = nullptr, *part_y = nullptr;
     double *b0_64 = nullptr, *av_64 = nullptr, *n2_64 = nullptr, *part_dx = nullptr, *ybuf = nullptr,
-           *dtmp = nullptr;
+           *dtmp = nullptr, *x64 = nullptr;
     float *scale = nullptr;
     PartStat *part_stat = nullptr;
     DevState *st = nullptr;
@@ -92,7 +92,8 @@ void free_all(nsli_solver *h)
     if (h->graph)
         cudaGraphExecDestroy(h->graph);
     void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
-                   h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags};
+                   h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags,
+                   (h->x64 != h->x) ? (void *)h->x64 : nullptr};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -174,6 +175,7 @@ ReduceArgs reduce_args(nsli_solver *h)
     a.part_y = h->part_y;
     a.part_stat = h->part_stat;
     a.x = h->x;
+    a.x64 = h->x64;
     a.ybuf = h->ybuf;
     a.part_dx = h->part_dx;
     a.st = h->st;
@@ -262,7 +264,7 @@ int run_verify(nsli_solver *h)
     CK(cudaMemsetAsync(h->ver, 0, sizeof(VerOut), h->stream), "clear check");
     VerifyArgs a;
     a.A = h->A;
-    a.x = h->x;
+    a.x64 = h->x64;
     a.b0_64 = h->b0_64;
     a.av_64 = h->av_64;
     a.n2_64 = h->n2_64;
@@ -391,6 +393,10 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
     if (storage == NSLI_FP8E4M3)
         CKC(cudaMalloc((void **)&h->scale, (size_t)m * 4), "allocate row scales");
     CKC(cudaMalloc(&h->x, (size_t)h->ld * accb), "allocate x");
+    if (storage == NSLI_F64)
+        h->x64 = static_cast<double *>(h->x);
+    else
+        CKC(cudaMalloc((void **)&h->x64, (size_t)h->ld * 8), "allocate binary64 x");
     CKC(cudaMalloc(&h->part_y, (size_t)h->G * h->ld * accb), "allocate partial sums");
     CKC(cudaMalloc((void **)&h->part_stat, (size_t)h->G * sizeof(PartStat)), "allocate partial stats");
     CKC(cudaMalloc((void **)&h->part_dx, (size_t)h->red_grid * 8), "allocate step partials");
@@ -418,7 +424,7 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
     // x0 -> accumulation type (the staging buffer is reused for the norms
     // only after this kernel has consumed it, in stream order)
     CKC(cudaMemcpyAsync(h->dtmp, x0, (size_t)n * 8, cudaMemcpyDefault, s), "copy x0");
-    CKC(x_from_f64_launch(storage == NSLI_F64, s, h->dtmp, h->x, n, h->ld, h->flags), "convert x0");
+    CKC(x_from_f64_launch(storage == NSLI_F64, s, h->dtmp, h->x64, h->x, n, h->ld, h->flags), "convert x0");
     h->launches += 1;
 
     const double *norms_dev = nullptr;
@@ -731,9 +737,7 @@ int nsli_get_x(nsli_handle h, double *x)
 {
     if (!h || !x)
         return NSLI_ERR_ARG;
-    CK(x_to_f64_launch(h->storage == NSLI_F64, h->stream, h->x, h->dtmp, h->n), "convert x");
-    h->launches += 1;
-    CK(cudaMemcpyAsync(x, h->dtmp, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
+    CK(cudaMemcpyAsync(x, h->x64, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
     return NSLI_OK;
 }
@@ -744,7 +748,8 @@ int nsli_set_x(nsli_handle h, const double *x)
         return NSLI_ERR_ARG;
     CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream), "clear flags");
     CK(cudaMemcpyAsync(h->dtmp, x, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
-    CK(x_from_f64_launch(h->storage == NSLI_F64, h->stream, h->dtmp, h->x, h->n, h->ld, h->flags), "convert x");
+    CK(x_from_f64_launch(h->storage == NSLI_F64, h->stream, h->dtmp, h->x64, h->x, h->n, h->ld, h->flags),
+       "convert x");
     h->launches += 1;
     return read_flags(h);
 }

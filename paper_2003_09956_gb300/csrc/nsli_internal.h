@@ -8,7 +8,9 @@
 //          and the FP8 row scale, in the accumulation type; the Map streams
 //          it beside the row.
 //   b0_64, av_64, n2_64   binary64 copies for the binary64 check.
-//   x      ld elements of the accumulation type (padding stays zero).
+//   x64    ld binary64 elements: the iterate itself, updated in binary64.
+//   x      ld elements of the accumulation type, the rounding of x64 that the
+//          Map reads (for binary64 storage the same buffer as x64).
 //   part_y G x ld partial sums of the positive slices, one row per CTA of
 //          the Map; part_stat G records (h, max r, max r/||a||, max |b|).
 #pragma once
@@ -82,7 +84,8 @@ struct MapArgs {
 struct ReduceArgs {
     const void *part_y;
     const PartStat *part_stat;
-    void *x;
+    void *x;               // accumulation-type copy read by the Map
+    double *x64;           // binary64 iterate
     double *ybuf;
     double *part_dx;
     DevState *st;
@@ -92,7 +95,7 @@ struct ReduceArgs {
 
 struct VerifyArgs {
     const void *A;
-    const void *x;
+    const double *x64;
     const double *b0_64, *av_64, *n2_64;
     const float *scale;    // per-row FP8 scale (NULL otherwise)
     const DevState *st;
@@ -139,9 +142,9 @@ struct MetaArgs {
 };
 cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a);
 
-cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, void *x,
+// x64[j] = src[j] (j < n), 0 up to ld; x = x64 rounded to the accumulation type
+cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, double *x64, void *x,
                               long long n, long long ld, int *flags);
-cudaError_t x_to_f64_launch(bool f64, cudaStream_t s, const void *x, double *dst, long long n);
 cudaError_t check_finite_launch(cudaStream_t s, const double *v, long long n, int *flags);
 
 struct StateBegin {

@@ -212,8 +212,9 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
     constexpr int EPV = Tr::EPV;
-    // rows per barrier: fewer when a thread already holds 32 row elements
-    constexpr int RG = (VPT * EPV >= 32) ? 2 : kMapRowGroup;
+    // rows per block barrier; with 8 vectors per thread a row is > 32 KB and
+    // a slot holds one row
+    constexpr int RG = (VPT >= 8) ? 1 : kMapRowGroup;
 
     DevState *st = p.st;
     if (!p.ignore_done && *(volatile int *)&st->done)
@@ -301,12 +302,20 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
 
         for (int g0 = 0; g0 < rows; g0 += RG) {
             const int gr = (rows - g0) < RG ? (rows - g0) : RG;
+            // per-thread partial dots in NCH independent FMA chains, added
+            // pairwise at the end (a fixed order); rows of > 32 KB (VPT = 8)
+            // leave enough time per row for a single chain
+            constexpr int NCH = (VPT >= 8) ? 1 : ((VPT >= 4) ? 4 : 2);
             Acc acc[RG];
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
                 acc[rr] = Acc(0);
                 if (rr < gr) {
                     const uint4 *rowv = reinterpret_cast<const uint4 *>(sbase + (size_t)(g0 + rr) * p.row_bytes);
+                    Acc part[NCH];
+#pragma unroll
+                    for (int q = 0; q < NCH; ++q)
+                        part[q] = Acc(0);
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) {
                         const int j = tid + v * nt;
@@ -314,20 +323,30 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
                             Acc a[EPV];
                             decode<S>(rowv[j], a);
 #pragma unroll
-                            for (int e = 0; e < EPV; ++e)
-                                acc[rr] = fma(a[e], xr[v][e], acc[rr]);
+                            for (int e = 0; e < EPV; ++e) {
+                                const int q = (NCH <= VPT) ? (v % NCH) : (e % NCH);
+                                part[q] = fma(a[e], xr[v][e], part[q]);
+                            }
                         }
                     }
+#pragma unroll
+                    for (int w2 = 1; w2 < NCH; w2 *= 2)
+#pragma unroll
+                        for (int q = 0; q + w2 < NCH; q += 2 * w2)
+                            part[q] += part[q + w2];
+                    acc[rr] = part[0];
                 }
             }
-            Acc *rb = red + (grp_counter & 1) * RG * 32;
+            Acc *rb = red + (grp_counter & 1) * kMapRowGroup * 32;
 #pragma unroll
-            for (int rr = 0; rr < RG; ++rr) {
-                if (rr < gr) {
-                    const Acc t = warp_sum(acc[rr]);
-                    if (lane == 0)
-                        rb[rr * 32 + warp] = t;
-                }
+            for (int rr = 0; rr < RG; ++rr)
+                if (rr < gr)
+                    acc[rr] = warp_sum(acc[rr]);
+            if (lane == 0) {
+#pragma unroll
+                for (int rr = 0; rr < RG; ++rr)
+                    if (rr < gr)
+                        rb[rr * 32 + warp] = acc[rr];
             }
             aborted = bar_all_or(nt, timed_out);
             if (aborted)
@@ -344,14 +363,23 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
                 }
             }
 
+            // block totals: lane w of every warp loads warp w's partial and a
+            // butterfly adds them, the same tree in every warp, so all
+            // threads hold bit-identical totals
+            Acc tot[RG];
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr)
+                tot[rr] = (rr < gr && lane < nwarps) ? rb[rr * 32 + lane] : Acc(0);
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr)
+                if (rr < gr)
+                    tot[rr] = warp_sum(tot[rr]);
             Acc c[RG];
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
                 c[rr] = Acc(0);
                 if (rr < gr) {
-                    Acc dot = Acc(0);
-                    for (int w = 0; w < nwarps; ++w)
-                        dot += rb[rr * 32 + w];
+                    const Acc dot = tot[rr];
                     const Meta md = smeta[g0 + rr];
                     const Acc sc = (Acc)meta_scale(md);
                     const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
@@ -520,11 +548,11 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
                 val = y * y;
             } else {
                 const double s = h > 0 ? lambda / (double)h : 0.0;
-                Acc *x = static_cast<Acc *>(p.x);
-                const Acc xo = x[j];
-                const Acc xn = (Acc)((double)xo - s * y);
-                x[j] = xn;
-                const double d = (double)xn - (double)xo;
+                const double xo = p.x64[j];
+                const double xn = xo - s * y;
+                p.x64[j] = xn;
+                static_cast<Acc *>(p.x)[j] = (Acc)xn;
+                const double d = xn - xo;
                 val = d * d;
             }
         }
@@ -561,10 +589,11 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
             Acc *x = static_cast<Acc *>(p.x);
             double v = 0.0;
             for (long long q = threadIdx.x; q < p.ld; q += blockDim.x) {
-                const Acc xo = x[q];
-                const Acc xn = (Acc)((double)xo - s * __ldcg(p.ybuf + q));
-                x[q] = xn;
-                const double d = (double)xn - (double)xo;
+                const double xo = p.x64[q];
+                const double xn = xo - s * __ldcg(p.ybuf + q);
+                p.x64[q] = xn;
+                x[q] = (Acc)xn;
+                const double d = xn - xo;
                 v += d * d;
             }
             v = warp_sum(v);
@@ -661,7 +690,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs p)
     const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const double kr = __dmul_rn((double)p.st->tick, p.st->rho);
-    const Acc *x = static_cast<const Acc *>(p.x);
+    const double *x = p.x64;
     const long long row_bytes = (long long)p.nv * 16;
     double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
     unsigned long long h = 0;
@@ -673,7 +702,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs p)
             decode<S>(__ldg(row + j), a);
 #pragma unroll
             for (int e = 0; e < EPV; ++e)
-                s = fma((double)a[e], (double)x[(long long)j * EPV + e], s);
+                s = fma((double)a[e], x[(long long)j * EPV + e], s);
         }
         s = warp_sum(s);
         if (S == NSLI_FP8E4M3)
@@ -825,7 +854,7 @@ __global__ void __launch_bounds__(256) meta_kernel(const MetaArgs p)
 }
 
 template <typename Acc>
-__global__ void x_from_f64_kernel(const double *src, Acc *x, long long n, long long ld, int *flags)
+__global__ void x_from_f64_kernel(const double *src, double *x64, Acc *x, long long n, long long ld, int *flags)
 {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ld)
@@ -836,15 +865,8 @@ __global__ void x_from_f64_kernel(const double *src, Acc *x, long long n, long l
         if (!isfinite(v))
             atomicOr(flags, PREPF_NONFINITE);
     }
+    x64[j] = v;
     x[j] = (Acc)v;
-}
-
-template <typename Acc>
-__global__ void x_to_f64_kernel(const Acc *x, double *dst, long long n)
-{
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n)
-        dst[j] = (double)x[j];
 }
 
 __global__ void check_finite_kernel(const double *v, long long n, int *flags)
@@ -1017,24 +1039,14 @@ cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a)
     return cudaGetLastError();
 }
 
-cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, void *x, long long n, long long ld,
-                              int *flags)
+cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, double *x64, void *x, long long n,
+                              long long ld, int *flags)
 {
     const unsigned int grid = (unsigned int)((ld + 255) / 256);
     if (f64)
-        x_from_f64_kernel<double><<<grid, 256, 0, s>>>(src, static_cast<double *>(x), n, ld, flags);
+        x_from_f64_kernel<double><<<grid, 256, 0, s>>>(src, x64, static_cast<double *>(x), n, ld, flags);
     else
-        x_from_f64_kernel<float><<<grid, 256, 0, s>>>(src, static_cast<float *>(x), n, ld, flags);
-    return cudaGetLastError();
-}
-
-cudaError_t x_to_f64_launch(bool f64, cudaStream_t s, const void *x, double *dst, long long n)
-{
-    const unsigned int grid = (unsigned int)((n + 255) / 256);
-    if (f64)
-        x_to_f64_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(x), dst, n);
-    else
-        x_to_f64_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(x), dst, n);
+        x_from_f64_kernel<float><<<grid, 256, 0, s>>>(src, x64, static_cast<float *>(x), n, ld, flags);
     return cudaGetLastError();
 }
 

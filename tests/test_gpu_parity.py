@@ -113,45 +113,54 @@ def test_map_reduce_after_tick_and_new_b(storage):
 
 # ------------------------------------------------------------------ trajectories
 
-def oracle_trajectory(A_eff, p, rule, lam, rho, K, storage):
-    """x_1..x_K of the oracle, and the first iteration whose Map had an
-    ambiguous row (comparison is only meaningful before it)."""
+def oracle_trajectory(A_eff, p, rule, lam, rho, K):
+    """x_0..x_K of the oracle and the residuals r(x_k, b(k)) of each Map."""
     n2, _ = oracle.norms2(A_eff)
-    xs, first_amb = [], K
+    xs, rs = [p["x0"].copy()], []
     x = p["x0"].copy()
     for k in range(K):
         code, x, st, y, r = oracle.iteration(A_eff, p["b0"], p["Av"], rho, k, n2, x,
                                              lam=lam, rule=rule)
-        b_k = oracle.tick_b(p["b0"], p["Av"], rho, k)
-        bound = ambiguity_bound(A_eff, xs[-1] if xs else p["x0"], b_k, U[storage]) * 100
-        if first_amb == K and np.any(np.abs(r) <= bound):
-            first_amb = k
         xs.append(x.copy())
-    return xs, first_amb
+        rs.append(r)
+    return xs, rs, n2
 
 
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("rule", ["relaxed", "modap"])
 @pytest.mark.parametrize("rho", [0.0, 1e-3])
 def test_trajectory_matches_oracle(storage, rule, rho):
-    m, n, K = 1500, 257, 15
+    """Iterates agree to 1e-5 relative (1e-12 for binary64 storage) at every
+    iteration, compared until the first Map with an ambiguous row: one whose
+    oracle residual is within the rounding bound plus ||a_i|| times the
+    current distance between the two iterates (from then on both
+    classifications, hence both trajectories, are correct)."""
+    m, n, K = 800, 257, 15
     p = workloads.dense_system(m, n, seed=5 + int(rho * 1e4))
     A_eff = stored_values(p["A"], storage)
     src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
     lam = 1.0 if rule == "relaxed" else 0.5
     orule = oracle.RULE_RELAXED if rule == "relaxed" else oracle.RULE_MODAP
-    xs, first_amb = oracle_trajectory(A_eff, p, orule, lam, rho, K, storage)
-    assert first_amb >= 3, "seeded case became ambiguous too early"
     tol = 1e-5 if storage != "f64" else 1e-12
+    xs, rs, n2 = oracle_trajectory(A_eff, p, orule, lam, rho, K)
+    compared = 0
     with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
-        for k in range(first_amb):
+        xg = s.get_x()
+        for k in range(K):
+            drift = np.linalg.norm(xg - xs[k])
+            b_k = oracle.tick_b(p["b0"], p["Av"], rho, k)
+            bound = ambiguity_bound(A_eff, xs[k], b_k, U[storage]) / 4 + \
+                np.sqrt(n2) * drift * 1.01
+            if np.any(np.abs(rs[k]) <= bound):
+                break
             s.iterate(1, lam=lam, rule=rule, rho=rho)
             xg = s.get_x()
-            rel = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+            rel = np.linalg.norm(xg - xs[k + 1]) / np.linalg.norm(xs[k + 1])
             assert rel <= tol, (k, rel)
+            compared += 1
+        assert compared >= 3, "seeded case became ambiguous too early"
         res = s.result()
-        assert res["iters"] == 1  # each iterate() call is one run of one update
-        assert res["tick"] == first_amb
+        assert res["tick"] == compared
 
 
 def test_graph_blocks_equal_single_launches():
