@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -23,6 +24,7 @@ struct nsli_solver {
     long long m = 0, n = 0, ld = 0;
     int elem_bytes = 4, epv = 4, row_bytes = 0, nv = 0;
     int vpt = 1, consumers = 32, R = 1, nstage = 2, stage_stride = 0;
+    bool guard = true;
     size_t smem = 0;
     int G = 1, red_grid = 1, num_sms = 1;
     long long rows_base = 0;
@@ -133,7 +135,16 @@ int choose_config(nsli_solver *h)
         return set_err(h, NSLI_ERR_UNSUPPORTED,
                        "n too large for the register-resident row kernel of this build");
     h->consumers = (int)round_up((h->nv + h->vpt - 1) / h->vpt, 32);
-    h->R = std::max(1, std::min(64, 65536 / h->row_bytes));
+    // bytes of A per ring slot: 64 KiB unless NSLI_MAP_SLOT_KB (4..96) overrides it
+    int slot_target = 65536;
+    if (const char *env = std::getenv("NSLI_MAP_SLOT_KB")) {
+        const int kb = std::atoi(env);
+        if (kb >= 4 && kb <= 96)
+            slot_target = kb * 1024;
+    }
+    h->guard = (long long)h->consumers * h->vpt != h->nv;
+    const int rg = map_rows_per_group(h->vpt);
+    h->R = rg * std::max(1, std::min(64 / rg, slot_target / (h->row_bytes * rg)));
     h->stage_stride = (int)round_up((long long)h->R * h->row_bytes + (long long)h->R * 32, 128);
     const int budget = 232448 - kSmemHeader;
     h->nstage = std::min(8, budget / h->stage_stride);
@@ -186,7 +197,7 @@ ReduceArgs reduce_args(nsli_solver *h)
 
 cudaError_t launch_iteration(nsli_solver *h)
 {
-    cudaError_t e = map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, map_args(h));
+    cudaError_t e = map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, map_args(h));
     if (e != cudaSuccess)
         return e;
     return reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
@@ -505,7 +516,7 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
         return fail(cuda_err(h, err, "prepare A"));
     if ((rc = read_flags(h)) != NSLI_OK)
         return fail(rc);
-    CKC(map_prepare(storage, h->vpt, h->smem), "configure Map kernel");
+    CKC(map_prepare(storage, h->vpt, h->guard, h->smem), "configure Map kernel");
 #undef CKC
     *out = h;
     return NSLI_OK;
@@ -607,7 +618,7 @@ int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter, doub
         const int cnt = (int)std::min<long long>(batch, n_iter - done);
         for (int i = 0; i < cnt && err == cudaSuccess; ++i) {
             cudaEventRecord(ev[3 * i], h->stream);
-            err = map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, map_args(h));
+            err = map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, map_args(h));
             if (err != cudaSuccess)
                 break;
             cudaEventRecord(ev[3 * i + 1], h->stream);
@@ -714,7 +725,7 @@ int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats)
         return NSLI_ERR_ARG;
     MapArgs ma = map_args(h);
     ma.ignore_done = 1;  // also after a finished run
-    CK(map_launch(h->storage, h->vpt, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
+    CK(map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
     CK(reduce_only_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h), h->ybuf),
        "launch Reduce");
     h->launches += 2;

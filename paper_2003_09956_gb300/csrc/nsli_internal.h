@@ -110,9 +110,14 @@ constexpr int kMapRowGroup = 4;      // rows reduced per block barrier
 constexpr int kReduceCols = 32;      // columns per reduce block
 constexpr int kSmemHeader = 2304;    // barriers, flags, warp-sum buffers
 
+// rows per block barrier of the Map kernel for a vectors-per-thread count;
+// a ring slot always holds a multiple of it
+__host__ __device__ constexpr int map_rows_per_group(int vpt) { return vpt >= 8 ? 1 : (vpt >= 4 ? 2 : 4); }
+
 int map_vpt_limit(int storage);      // largest vectors-per-thread instance
-cudaError_t map_prepare(int storage, int vpt, size_t smem);
-cudaError_t map_launch(int storage, int vpt, int grid, int consumers, size_t smem,
+// guard: some thread's vectors fall outside the row (nv < threads * vpt)
+cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem);
+cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers, size_t smem,
                        cudaStream_t s, const MapArgs &a);
 cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a);
 cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a,

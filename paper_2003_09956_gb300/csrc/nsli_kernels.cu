@@ -102,17 +102,9 @@ template <> __device__ __forceinline__ void decode<NSLI_FP8E4M3>(const uint4 q, 
 
 // ------------------------------------------------ barriers and bulk copies --
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
-
 __device__ __forceinline__ unsigned int smem_u32(const void *p)
 {
     return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 __device__ __forceinline__ void mbar_init(unsigned int bar, unsigned int count)
 {
@@ -127,32 +119,30 @@ __device__ __forceinline__ void mbar_arrive(unsigned int bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(unsigned int bar, unsigned int parity)
+__device__ __forceinline__ bool mbar_test(unsigned int bar, unsigned int parity)
 {
     unsigned int ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity to complete; gives up after the
-// time limit or when *abort_flag becomes non-zero.  Returns true on success.
-__device__ __noinline__ bool mbar_wait_bounded(unsigned int bar, unsigned int parity,
-                                               volatile int *abort_flag)
+// Wait for the phase of the given parity to complete by polling (a
+// non-suspending test: the waiting warps resume as soon as the phase
+// completes).  Gives up after kWaitLimitCycles SM cycles (about two seconds
+// at the maximum clock), checked every 256 polls.  Returns true on success.
+constexpr long long kWaitLimitCycles = 4000000000ll;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned int bar, unsigned int parity)
 {
-    if (mbar_try_wait(bar, parity))
-        return true;
-    const unsigned long long t0 = gtimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity))
+    const long long t0 = clock64();
+    for (unsigned int it = 0;; ++it) {
+        if (mbar_test(bar, parity))
             return true;
-        if (abort_flag != nullptr && *abort_flag)
-            return false;
-        if (gtimer() - t0 > kWaitLimitNs)
+        if ((it & 255u) == 255u && clock64() - t0 > kWaitLimitCycles)
             return false;
     }
 }
@@ -188,6 +178,25 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// d0 += a0 * b0 and d1 += a1 * b1 with one packed binary32x2 FMA
+// (round to nearest; the same result as two scalar fmaf).
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rd, {%0, %1};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma2(double &d0, double &d1, double a0, double a1, double b0, double b1)
+{
+    d0 = fma(a0, b0, d0);
+    d1 = fma(a1, b1, d1);
+}
+
 template <typename T> __device__ __forceinline__ T neg_inf();
 template <> __device__ __forceinline__ float neg_inf<float>() { return -INFINITY; }
 template <> __device__ __forceinline__ double neg_inf<double>() { return -INFINITY; }
@@ -201,20 +210,59 @@ template <> __device__ __forceinline__ double neg_inf<double>() { return -INFINI
 // front, then, right after the first barrier of slot s, the refill of the
 // stage that slot s-1 released (every warp released it before reaching that
 // barrier, so the wait is immediate).
-// Per group of up to 4 rows: per-thread partial dots, warp butterfly, one
-// barrier, every thread sums the warp totals in the same order (so all
-// threads hold bit-identical r_i), then the violated rows are added into
-// the y registers from the same shared-memory copy of the row.
-template <int S, int VPT>
+//
+// Rows are handled in groups of RG (compile time; a slot holds a multiple of
+// RG rows, rows past the CTA's end are masked).  Per group: per-thread
+// partial dots (packed FMAs), a transposed warp reduction that folds the RG
+// rows into one butterfly (lanes [q*32/RG, (q+1)*32/RG) end with row q), one
+// barrier, a second transposed reduction of the per-warp totals that every
+// warp performs in the same order (so all threads hold bit-identical r_i),
+// then the violated rows are added into the y registers from the same
+// shared-memory copy of the row.  GUARD = false when every thread's vectors
+// lie inside the row (no per-vector bounds tests).
+
+// Sum v[0..RG) over the warp with one folded butterfly; returns, in lane l,
+// the warp total of row l / (32 / RG).
+template <int RG, typename T> __device__ __forceinline__ T warp_fold_rows(const T (&v)[RG], int lane)
+{
+    if constexpr (RG == 1) {
+        return warp_sum(v[0]);
+    } else if constexpr (RG == 2) {
+        const bool hi = (lane & 16) != 0;
+        T keep = hi ? v[1] : v[0];
+        const T send = hi ? v[0] : v[1];
+        keep += __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1)
+            keep += __shfl_xor_sync(0xffffffffu, keep, off);
+        return keep;
+    } else {
+        static_assert(RG == 4, "row groups of 1, 2 or 4");
+        const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+        T k0 = b4 ? v[2] : v[0], k1 = b4 ? v[3] : v[1];
+        const T s0 = b4 ? v[0] : v[2], s1 = b4 ? v[1] : v[3];
+        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+        T keep = b3 ? k1 : k0;
+        const T send = b3 ? k0 : k1;
+        keep += __shfl_xor_sync(0xffffffffu, send, 8);
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1)
+            keep += __shfl_xor_sync(0xffffffffu, keep, off);
+        return keep;
+    }
+}
+
+template <int S, int VPT, bool GUARD>
 __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs p)
 {
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
     constexpr int EPV = Tr::EPV;
-    // rows per block barrier; with 8 vectors per thread a row is > 32 KB and
-    // a slot holds one row
-    constexpr int RG = (VPT >= 8) ? 1 : kMapRowGroup;
+    constexpr int RG = map_rows_per_group(VPT);
+    constexpr int W = 32 / RG;                 // lanes per row in the folded reductions
+    constexpr int NCH = (VPT >= 4 && RG <= 2) ? 2 : 1;  // independent chains per row
 
     DevState *st = p.st;
     if (!p.ignore_done && *(volatile int *)&st->done)
@@ -222,7 +270,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);  // full[8], empty[8]
-    Acc *red = reinterpret_cast<Acc *>(smem + 256);                          // [2][RG][32]
+    Acc *red = reinterpret_cast<Acc *>(smem + 256);                          // [2][4][32]
     unsigned char *stages = smem + kSmemHeader;
 
     const int tid = threadIdx.x;
@@ -268,6 +316,16 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     }
     __syncthreads();
 
+    // shared-memory byte offsets of this thread's vectors within a row
+    int voff[VPT];
+    bool vok[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int j = tid + v * nt;
+        voff[v] = j * 16;
+        vok[v] = !GUARD || j < p.nv;
+    }
+
     Acc xr[VPT][EPV];
     Acc yr[VPT][EPV];
     {
@@ -277,7 +335,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
             const int j = tid + v * nt;
 #pragma unroll
             for (int e = 0; e < EPV; ++e) {
-                xr[v][e] = (j < p.nv) ? xg[(long long)j * EPV + e] : Acc(0);
+                xr[v][e] = vok[v] ? xg[(long long)j * EPV + e] : Acc(0);
                 yr[v][e] = Acc(0);
             }
         }
@@ -293,7 +351,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     for (int s = 0; s < nslots; ++s) {
         const int stage = s % p.nstage;
         const unsigned int ph = (unsigned int)((s / p.nstage) & 1);
-        int timed_out = mbar_wait_bounded(smem_u32(&bars[stage]), ph, nullptr) ? 0 : 1;
+        int timed_out = mbar_wait_bounded(smem_u32(&bars[stage]), ph) ? 0 : 1;
         const unsigned char *sbase = stages + (size_t)stage * p.stage_stride;
         const Meta *smeta = reinterpret_cast<const Meta *>(sbase + (size_t)R * p.row_bytes);
         const long long r0 = row_begin + (long long)s * R;
@@ -301,53 +359,37 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
         const int rows = (int)(left < R ? left : R);
 
         for (int g0 = 0; g0 < rows; g0 += RG) {
-            const int gr = (rows - g0) < RG ? (rows - g0) : RG;
-            // per-thread partial dots in NCH independent FMA chains, added
-            // pairwise at the end (a fixed order); rows of > 32 KB (VPT = 8)
-            // leave enough time per row for a single chain
-            constexpr int NCH = (VPT >= 8) ? 1 : ((VPT >= 4) ? 4 : 2);
+            // ---- per-thread partial dots of the RG rows of this group
             Acc acc[RG];
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
-                acc[rr] = Acc(0);
-                if (rr < gr) {
-                    const uint4 *rowv = reinterpret_cast<const uint4 *>(sbase + (size_t)(g0 + rr) * p.row_bytes);
-                    Acc part[NCH];
+                const unsigned char *row = sbase + (size_t)(g0 + rr) * p.row_bytes;
+                Acc pe[NCH], po[NCH];
 #pragma unroll
-                    for (int q = 0; q < NCH; ++q)
-                        part[q] = Acc(0);
-#pragma unroll
-                    for (int v = 0; v < VPT; ++v) {
-                        const int j = tid + v * nt;
-                        if (j < p.nv) {
-                            Acc a[EPV];
-                            decode<S>(rowv[j], a);
-#pragma unroll
-                            for (int e = 0; e < EPV; ++e) {
-                                const int q = (NCH <= VPT) ? (v % NCH) : (e % NCH);
-                                part[q] = fma(a[e], xr[v][e], part[q]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int w2 = 1; w2 < NCH; w2 *= 2)
-#pragma unroll
-                        for (int q = 0; q + w2 < NCH; q += 2 * w2)
-                            part[q] += part[q + w2];
-                    acc[rr] = part[0];
+                for (int q = 0; q < NCH; ++q) {
+                    pe[q] = Acc(0);
+                    po[q] = Acc(0);
                 }
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    if (vok[v]) {
+                        Acc a[EPV];
+                        decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+#pragma unroll
+                        for (int e = 0; e < EPV; e += 2)
+                            fma2(pe[v % NCH], po[v % NCH], a[e], a[e + 1], xr[v][e], xr[v][e + 1]);
+                    }
+                }
+                Acc t = pe[0] + po[0];
+#pragma unroll
+                for (int q = 1; q < NCH; ++q)
+                    t += pe[q] + po[q];
+                acc[rr] = t;
             }
             Acc *rb = red + (grp_counter & 1) * kMapRowGroup * 32;
-#pragma unroll
-            for (int rr = 0; rr < RG; ++rr)
-                if (rr < gr)
-                    acc[rr] = warp_sum(acc[rr]);
-            if (lane == 0) {
-#pragma unroll
-                for (int rr = 0; rr < RG; ++rr)
-                    if (rr < gr)
-                        rb[rr * 32 + warp] = acc[rr];
-            }
+            const Acc wsum = warp_fold_rows<RG>(acc, lane);
+            if ((lane & (W - 1)) == 0)
+                rb[(lane / W) * 32 + warp] = wsum;
             aborted = bar_all_or(nt, timed_out);
             if (aborted)
                 break;
@@ -355,73 +397,69 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
                 // slot s-1 was released by every warp before this barrier
                 const int sp = s - 1;
                 if (mbar_wait_bounded(smem_u32(&bars[8 + sp % p.nstage]),
-                                      (unsigned int)((sp / p.nstage) & 1), nullptr)) {
+                                      (unsigned int)((sp / p.nstage) & 1))) {
                     issue(issued);
                     ++issued;
                 } else {
-                    timed_out = 1;  // reported at the next barrier
+                    timed_out = 1;  // reported below
                 }
             }
 
-            // block totals: lane w of every warp loads warp w's partial and a
-            // butterfly adds them, the same tree in every warp, so all
-            // threads hold bit-identical totals
-            Acc tot[RG];
+            // ---- block totals: lane (q, i) adds the partials of warps
+            // i, i + W, ... of row q; every warp runs the same tree
+            Acc tsum = Acc(0);
+            {
+                const int q = lane / W, i = lane % W;
+                for (int w = i; w < nwarps; w += W)
+                    tsum += rb[q * 32 + w];
 #pragma unroll
-            for (int rr = 0; rr < RG; ++rr)
-                tot[rr] = (rr < gr && lane < nwarps) ? rb[rr * 32 + lane] : Acc(0);
-#pragma unroll
-            for (int rr = 0; rr < RG; ++rr)
-                if (rr < gr)
-                    tot[rr] = warp_sum(tot[rr]);
+                for (int off = W / 2; off > 0; off >>= 1)
+                    tsum += __shfl_xor_sync(0xffffffffu, tsum, off);
+            }
             Acc c[RG];
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
-                c[rr] = Acc(0);
-                if (rr < gr) {
-                    const Acc dot = tot[rr];
-                    const Meta md = smeta[g0 + rr];
-                    const Acc sc = (Acc)meta_scale(md);
-                    const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
-                    const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
-                    if (ri > Acc(0))
-                        c[rr] = (S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2;
-                    if (tid == 0) {
-                        h_loc += (ri > Acc(0)) ? 1 : 0;
-                        mv = ri > mv ? ri : mv;
-                        const Acc rn = ri * (Acc)md.inv_n;
-                        mn = rn > mn ? rn : mn;
-                        const Acc ab = bi < Acc(0) ? -bi : bi;
-                        mb = ab > mb ? ab : mb;
-                    }
+                const Acc dot = (RG == 1) ? tsum : __shfl_sync(0xffffffffu, tsum, rr * W);
+                const bool valid = (g0 + rr) < rows;
+                const Meta md = smeta[valid ? g0 + rr : 0];
+                const Acc sc = (Acc)meta_scale(md);
+                const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
+                const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
+                const bool viol = valid && ri > Acc(0);
+                c[rr] = viol ? ((S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2) : Acc(0);
+                if (warp == 0 && valid) {  // warp-uniform; thread 0 writes them out
+                    h_loc += viol ? 1 : 0;
+                    mv = ri > mv ? ri : mv;
+                    const Acc rn = ri * (Acc)md.inv_n;
+                    mn = rn > mn ? rn : mn;
+                    const Acc ab = bi < Acc(0) ? -bi : bi;
+                    mb = ab > mb ? ab : mb;
                 }
             }
+            // ---- add the positive slices of the violated rows
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
-                if (rr < gr && c[rr] != Acc(0)) {
-                    const uint4 *rowv = reinterpret_cast<const uint4 *>(sbase + (size_t)(g0 + rr) * p.row_bytes);
+                if (c[rr] != Acc(0)) {
+                    const unsigned char *row = sbase + (size_t)(g0 + rr) * p.row_bytes;
                     const Acc cr = c[rr];
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) {
-                        const int j = tid + v * nt;
-                        if (j < p.nv) {
+                        if (vok[v]) {
                             Acc a[EPV];
-                            decode<S>(rowv[j], a);
+                            decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
 #pragma unroll
-                            for (int e = 0; e < EPV; ++e)
-                                yr[v][e] = fma(cr, a[e], yr[v][e]);
+                            for (int e = 0; e < EPV; e += 2)
+                                fma2(yr[v][e], yr[v][e + 1], cr, cr, a[e], a[e + 1]);
                         }
                     }
                 }
             }
             ++grp_counter;
+            if (timed_out && tid == 0)
+                atomicOr(&st->error, ERRF_TIMEOUT);
         }
         if (aborted)
             break;
-        // a refill wait that gave up is voted on at the next barrier; with no
-        // barrier left in this CTA it is reported directly
-        if (timed_out && tid == 0)
-            atomicOr(&st->error, ERRF_TIMEOUT);
         __syncwarp();
         if (lane == 0)
             mbar_arrive(smem_u32(&bars[8 + stage]));
@@ -434,7 +472,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
         if (tid == 0) {
             atomicOr(&st->error, ERRF_TIMEOUT);
             for (int s = consumed; s < issued; ++s)
-                mbar_wait_bounded(smem_u32(&bars[s % p.nstage]), (unsigned int)((s / p.nstage) & 1), nullptr);
+                mbar_wait_bounded(smem_u32(&bars[s % p.nstage]), (unsigned int)((s / p.nstage) & 1));
         }
         return;
     }
@@ -442,11 +480,11 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     Acc *py = static_cast<Acc *>(p.part_y) + (long long)blockIdx.x * p.ld;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        const int j = tid + v * nt;
-        if (j < p.nv) {
+        if (vok[v]) {
+            const long long j = tid + v * nt;
 #pragma unroll
             for (int e = 0; e < EPV; ++e)
-                py[(long long)j * EPV + e] = yr[v][e];
+                py[j * EPV + e] = yr[v][e];
         }
     }
     if (tid == 0) {
@@ -940,46 +978,46 @@ int map_vpt_limit(int storage)
     }
 }
 
-template <int S> static const void *map_fn(int vpt)
+template <int S, bool G> static const void *map_fn(int vpt)
 {
     switch (vpt) {
-    case 1: return (const void *)map_kernel<S, 1>;
-    case 2: return (const void *)map_kernel<S, 2>;
+    case 1: return (const void *)map_kernel<S, 1, G>;
+    case 2: return (const void *)map_kernel<S, 2, G>;
     case 4:
         if constexpr (S != NSLI_FP8E4M3)
-            return (const void *)map_kernel<S, 4>;
+            return (const void *)map_kernel<S, 4, G>;
         return nullptr;
     case 8:
         if constexpr (S == NSLI_F64 || S == NSLI_F32)
-            return (const void *)map_kernel<S, 8>;
+            return (const void *)map_kernel<S, 8, G>;
         return nullptr;
     default: return nullptr;
     }
 }
 
-static const void *map_fn_any(int storage, int vpt)
+static const void *map_fn_any(int storage, int vpt, bool guard)
 {
     switch (storage) {
-    case NSLI_F64: return map_fn<NSLI_F64>(vpt);
-    case NSLI_F32: return map_fn<NSLI_F32>(vpt);
-    case NSLI_BF16: return map_fn<NSLI_BF16>(vpt);
-    case NSLI_FP8E4M3: return map_fn<NSLI_FP8E4M3>(vpt);
+    case NSLI_F64: return guard ? map_fn<NSLI_F64, true>(vpt) : map_fn<NSLI_F64, false>(vpt);
+    case NSLI_F32: return guard ? map_fn<NSLI_F32, true>(vpt) : map_fn<NSLI_F32, false>(vpt);
+    case NSLI_BF16: return guard ? map_fn<NSLI_BF16, true>(vpt) : map_fn<NSLI_BF16, false>(vpt);
+    case NSLI_FP8E4M3: return guard ? map_fn<NSLI_FP8E4M3, true>(vpt) : map_fn<NSLI_FP8E4M3, false>(vpt);
     default: return nullptr;
     }
 }
 
-cudaError_t map_prepare(int storage, int vpt, size_t smem)
+cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
 {
-    const void *fn = map_fn_any(storage, vpt);
+    const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)
         return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t map_launch(int storage, int vpt, int grid, int consumers, size_t smem, cudaStream_t s,
+cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers, size_t smem, cudaStream_t s,
                        const MapArgs &a)
 {
-    const void *fn = map_fn_any(storage, vpt);
+    const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)
         return cudaErrorInvalidValue;
     void *args[] = {const_cast<MapArgs *>(&a)};
