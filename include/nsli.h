@@ -182,6 +182,29 @@ int nsli_get_norms2(nsli_handle h, double *out);
  * binary64 fields of out are those of the last check made, or 0.  Synchronises. */
 int nsli_get_result(nsli_handle h, nsli_result *out);
 
+/* Map + Reduce of a caller-held binary32 system that ALLOCATES NOTHING (the
+ * paper has no counterpart; this is an interface for callers that cannot
+ * allocate device memory: code running while a stream is captured into a
+ * CUDA graph, and code under a fixed memory budget or a host framework's own
+ * allocator).  With r_i = <a_i, x> - b_i it writes
+ *   y[j]       = sum over r_i > 0 of r_i / norms2[i] * a_ij   (n doubles),
+ *   *violated  = #{i : r_i > 0},  *max_viol = max_i r_i  (binary32 sums).
+ * Every pointer is a device pointer of the current device: A row-major, m
+ * rows of lda >= n floats; b, norms2: m floats (norms2[i] = ||a_i||^2 > 0);
+ * x: n floats.  Work is issued on `stream` (a cudaStream_t or NULL) and not
+ * synchronised.  Scratch: a fixed 4 MiB array (plus 16 KiB of counters)
+ * inside the library, held by every GPU that loads it until the process
+ * exits; n larger than 2^20 is rejected with NSLI_ERR_UNSUPPORTED.  The
+ * first call on a device looks up that array's device address (once per
+ * device), so make it before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race and must not be issued.
+ * Calls no cudaMalloc or cudaFree.  Returns NSLI_OK, NSLI_ERR_ARG,
+ * NSLI_ERR_UNSUPPORTED or NSLI_ERR_CUDA. */
+int nsli_map_reduce_noalloc(int64_t m, int64_t n, const float *A, int64_t lda,
+                            const float *b, const float *norms2, const float *x,
+                            double *y, int64_t *violated, double *max_viol,
+                            void *stream);
+
 /* Number of kernels the handle has launched so far (graph nodes included). */
 int64_t nsli_launch_count(nsli_handle h);
 

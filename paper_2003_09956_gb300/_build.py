@@ -1,6 +1,6 @@
 """Compile the CUDA library ``libnsli.so`` in-tree for sm_103a.
 
-nvcc cross-compiles on a machine without a GPU.  The two translation units
+nvcc cross-compiles on a machine without a GPU.  The translation units
 are compiled in parallel and linked with the static CUDA runtime.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libnsli.so")
-SOURCES = ["nsli_kernels.cu", "nsli_api.cu"]
+SOURCES = ["nsli_kernels.cu", "nsli_api.cu", "nsli_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "nsli_internal.h"), os.path.join(INCLUDE, "nsli.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

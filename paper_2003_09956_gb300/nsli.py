@@ -65,7 +65,7 @@ EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed",
            "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
            "nsli_get_stored_rows", "nsli_get_norms2",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
-           "nsli_strerror", "nsli_last_error"]
+           "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc"]
 
 
 def library_path() -> str:
@@ -120,6 +120,8 @@ def load(path: str | None = None):
         lib.nsli_strerror.restype = ctypes.c_char_p
         lib.nsli_last_error.argtypes = [H]
         lib.nsli_last_error.restype = ctypes.c_char_p
+        lib.nsli_map_reduce_noalloc.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, P]
+        lib.nsli_map_reduce_noalloc.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -175,6 +177,17 @@ def _sync_torch_inputs(*arrays):
             import torch
             torch.cuda.current_stream(a.device).synchronize()
             return
+
+
+def map_reduce_noalloc(A, b, norms2, x, y, violated, max_viol, stream=None):
+    """Allocation-free Map + Reduce on caller-held CUDA tensors (all float32
+    inputs, outputs y float64[n], violated int64[1], max_viol float64[1]).
+    For callers that cannot allocate device memory; see include/nsli.h."""
+    m, n = int(A.shape[0]), int(A.shape[1])
+    rc = load().nsli_map_reduce_noalloc(m, n, _ptr(A), int(A.stride(0)), _ptr(b), _ptr(norms2),
+                                        _ptr(x), _ptr(y), _ptr(violated), _ptr(max_viol),
+                                        None if stream is None else ctypes.c_void_p(stream))
+    _check(rc, "nsli_map_reduce_noalloc")
 
 
 def make_params(lam=1.0, rule="relaxed", stop="none", eps=0.0, max_iter=0,
