@@ -205,6 +205,48 @@ int nsli_map_reduce_noalloc(int64_t m, int64_t n, const float *A, int64_t lda,
                             double *y, int64_t *violated, double *max_viol,
                             void *stream);
 
+/* ---- Batched form: P <= 64 problems sharing one matrix (tensor cores) ----
+ * Problem p is A x <= b0 + (s_p + k) rho Av with its own x_p and tick
+ * offset s_p; all problems advance one tick per batch iteration.  Each batch
+ * iteration is the relaxed step of Algorithm 1 (Section 2, Eq. 7, Eq. 8)
+ * for every problem, computed as two tensor-core contractions R = A X and
+ * Y = A^T W over one bf16 copy of A (and its transpose), binary32
+ * accumulation. */
+typedef struct nsli_batch_solver *nsli_batch;
+
+/* A: host or device, m x n binary32 (row pitch lda), stored as bf16 (round
+ * to nearest even).  b0, Av (NULL: stationary): m doubles.  tick_offsets:
+ * nprob int64 s_p (NULL: all 0).  X0: nprob x n doubles, row-major.  stream:
+ * a non-default cudaStream_t or NULL (the handle then owns one).  Errors as
+ * nsli_create; NSLI_ERR_UNSUPPORTED for nprob > 64. */
+int nsli_batch_create(nsli_batch *out, int64_t m, int64_t n, int32_t nprob,
+                      const float *A, int64_t lda, const double *b0,
+                      const double *Av, const int64_t *tick_offsets,
+                      const double *X0, void *stream);
+
+/* n_iter batch iterations with lambda = p->lambda and rho = p->rho (RELAXED
+ * only; other fields ignored), graph-replayed in blocks of p->block_iters
+ * (0: 16).  Asynchronous. */
+int nsli_batch_iterate(nsli_batch h, const nsli_params *p, int64_t n_iter);
+
+/* One Map + Reduce for every problem at the current x and tick, no step:
+ * Y (host or device, nprob x n doubles), violated (host, nprob), max_viol
+ * (host, nprob; binary32 residuals).  Any output may be NULL.  Synchronises. */
+int nsli_batch_map_reduce(nsli_batch h, double rho, double *Y, int64_t *violated,
+                          double *max_viol);
+
+/* Current iterates (host or device, nprob x n doubles).  Synchronises. */
+int nsli_batch_get_x(nsli_batch h, double *X);
+
+/* Binary64 check per problem (Eq. 10): max_viol[p] = max_i r_i of problem p
+ * at its current tick (host, nprob doubles).  Synchronises. */
+int nsli_batch_residual_max(nsli_batch h, double *max_viol);
+
+int64_t nsli_batch_launch_count(nsli_batch h);
+int nsli_batch_sync(nsli_batch h);
+void nsli_batch_destroy(nsli_batch h);
+const char *nsli_batch_last_error(nsli_batch h);
+
 /* Number of kernels the handle has launched so far (graph nodes included). */
 int64_t nsli_launch_count(nsli_handle h);
 

@@ -65,7 +65,10 @@ EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed",
            "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
            "nsli_get_stored_rows", "nsli_get_norms2",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
-           "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc"]
+           "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc",
+           "nsli_batch_create", "nsli_batch_iterate", "nsli_batch_map_reduce", "nsli_batch_get_x",
+           "nsli_batch_residual_max", "nsli_batch_launch_count", "nsli_batch_sync",
+           "nsli_batch_destroy", "nsli_batch_last_error"]
 
 
 def library_path() -> str:
@@ -122,6 +125,24 @@ def load(path: str | None = None):
         lib.nsli_last_error.restype = ctypes.c_char_p
         lib.nsli_map_reduce_noalloc.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, P]
         lib.nsli_map_reduce_noalloc.restype = ctypes.c_int
+        lib.nsli_batch_create.argtypes = [ctypes.POINTER(H), i64, i64, i32, P, i64, P, P, P, P, P]
+        lib.nsli_batch_create.restype = ctypes.c_int
+        lib.nsli_batch_iterate.argtypes = [H, ctypes.POINTER(nsli_params), i64]
+        lib.nsli_batch_iterate.restype = ctypes.c_int
+        lib.nsli_batch_map_reduce.argtypes = [H, d, P, P, P]
+        lib.nsli_batch_map_reduce.restype = ctypes.c_int
+        lib.nsli_batch_get_x.argtypes = [H, P]
+        lib.nsli_batch_get_x.restype = ctypes.c_int
+        lib.nsli_batch_residual_max.argtypes = [H, P]
+        lib.nsli_batch_residual_max.restype = ctypes.c_int
+        lib.nsli_batch_launch_count.argtypes = [H]
+        lib.nsli_batch_launch_count.restype = i64
+        lib.nsli_batch_sync.argtypes = [H]
+        lib.nsli_batch_sync.restype = ctypes.c_int
+        lib.nsli_batch_destroy.argtypes = [H]
+        lib.nsli_batch_destroy.restype = None
+        lib.nsli_batch_last_error.argtypes = [H]
+        lib.nsli_batch_last_error.restype = ctypes.c_char_p
         if path is None:
             _lib = lib
         return lib
@@ -332,3 +353,75 @@ class Solver:
 
     def sync(self):
         _check(load().nsli_sync(self._h), "nsli_sync", self._h)
+
+
+class BatchSolver:
+    """P <= 64 problems sharing one matrix, iterated together on the tensor
+    cores (nsli_batch_*).  A: (m, n) float32; b0, Av: length m; X0: (P, n);
+    tick_offsets: length-P integers s_p (problem p sees b0 + (s_p + k) rho Av)."""
+
+    def __init__(self, A, b0, X0, Av=None, tick_offsets=None, stream=None):
+        lib = load()
+        A = np.ascontiguousarray(A, dtype=np.float32) if isinstance(A, np.ndarray) else A.contiguous()
+        m, n = int(A.shape[0]), int(A.shape[1])
+        X0 = np.ascontiguousarray(X0, dtype=np.float64) if isinstance(X0, np.ndarray) else \
+            X0.to(__import__("torch").float64).contiguous()
+        P = int(X0.shape[0])
+        b0, Av = _f64(b0, m), _f64(Av, m)
+        offs = None if tick_offsets is None else np.ascontiguousarray(tick_offsets, dtype=np.int64)
+        _sync_torch_inputs(A, b0, X0, Av)
+        h = ctypes.c_void_p()
+        rc = lib.nsli_batch_create(ctypes.byref(h), m, n, P, _ptr(A), n, _ptr(b0), _ptr(Av),
+                                   _ptr(offs), _ptr(X0), None if stream is None else ctypes.c_void_p(stream))
+        if rc != OK:
+            raise NsliError(rc, "nsli_batch_create")
+        self._h, self.m, self.n, self.P = h, m, n, P
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nsli_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, where):
+        if rc < 0:
+            raise NsliError(rc, where, load().nsli_batch_last_error(self._h).decode())
+
+    def iterate(self, n_iter, lam=1.0, rho=0.0, block_iters=0):
+        p = make_params(lam=lam, rho=rho, block_iters=block_iters)
+        self._check(load().nsli_batch_iterate(self._h, ctypes.byref(p), int(n_iter)), "nsli_batch_iterate")
+
+    def map_reduce(self, rho=0.0):
+        Y = np.empty((self.P, self.n), np.float64)
+        hv = np.empty(self.P, np.int64)
+        mv = np.empty(self.P, np.float64)
+        self._check(load().nsli_batch_map_reduce(self._h, float(rho), _ptr(Y), _ptr(hv), _ptr(mv)),
+                    "nsli_batch_map_reduce")
+        return Y, hv, mv
+
+    def get_x(self):
+        X = np.empty((self.P, self.n), np.float64)
+        self._check(load().nsli_batch_get_x(self._h, _ptr(X)), "nsli_batch_get_x")
+        return X
+
+    def residual_max(self):
+        mv = np.empty(self.P, np.float64)
+        self._check(load().nsli_batch_residual_max(self._h, _ptr(mv)), "nsli_batch_residual_max")
+        return mv
+
+    def launch_count(self) -> int:
+        return int(load().nsli_batch_launch_count(self._h))
+
+    def sync(self):
+        self._check(load().nsli_batch_sync(self._h), "nsli_batch_sync")
