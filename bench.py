@@ -41,6 +41,12 @@ WORKLOADS = {
     "dense-32768x16384": {"m": 32768, "n": 16384, "rho": 1e-4, "seed": 2006},
 }
 ELEM_BYTES = {"f32": 4, "bf16": 2, "fp8": 1, "f64": 8}
+BATCHED = {
+    # P problems sharing one bf16 A; problem p sees b0 + (p + k) rho Av
+    "batched-65536x8192x64": {"m": 65536, "n": 8192, "P": 64, "rho": 1e-4, "seed": 2007},
+    # a quarter of the rows, for profiler captures (A = 256 MiB bf16 > L2)
+    "batched-16384x8192x64": {"m": 16384, "n": 8192, "P": 64, "rho": 1e-4, "seed": 2009},
+}
 METRIC = "ModAP iterations/sec"
 UNIT = "iterations/s"
 
@@ -55,6 +61,10 @@ def parse_args():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--variants", default="bf16,fp8",
                     help="other storage types measured in the same run ('' for none)")
+    ap.add_argument("--batched", default="batched-65536x8192x64",
+                    help="batched tensor-core workload measured in the same run ('' for none)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the batched workload (profiling entry)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -176,6 +186,40 @@ def cpu_baseline(p, m_full, seconds, rho):
                                                                       rows, m_full)}
 
 
+def time_batched(nsli, torch, name, steps, warmup):
+    """Batch iterations of P problems sharing one bf16 A on the tensor cores."""
+    from paper_2003_09956_gb300 import workloads
+
+    w = BATCHED[name]
+    m, n, P = w["m"], w["n"], w["P"]
+    p = workloads.dense_system(m, n, seed=w["seed"])
+    rng = np.random.default_rng(w["seed"] + 1)
+    X0 = rng.normal(0.0, 5.0, (P, n)).astype(np.float32).astype(np.float64)
+    stream = torch.cuda.Stream()
+    bs = nsli.BatchSolver(p["A"], p["b0"], X0, Av=p["Av"], tick_offsets=np.arange(P), stream=stream.cuda_stream)
+    B = 16
+    bs.iterate(max(warmup, B), rho=w["rho"], block_iters=B)
+    bs.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = bs.launch_count()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        bs.iterate(steps, rho=w["rho"], block_iters=B)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = bs.launch_count() - l0
+    mv = bs.residual_max()
+    bs.close()
+    abytes = 2 * m * n * 2                 # A and its transpose, bf16, once each
+    flops = 2 * 2 * m * n * 3 * P          # two GEMMs, N = 3 split columns per problem
+    return {"workload": name, "batch_iterations_per_s": 1000.0 / ms, "problem_iterations_per_s": P * 1000.0 / ms,
+            "ms_per_batch_iteration": ms, "A_stream_gbs": abytes / (ms / 1e3) / 1e9,
+            "tensor_tflops": flops / (ms / 1e3) / 1e12, "gpu_launches": launches,
+            "max_viol_f64_first_problems": [float(v) for v in mv[:4]]}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,6 +312,13 @@ def main():
     from paper_2003_09956_gb300 import nsli, workloads
 
     nsli.load()
+    if args.batched_only:
+        r = time_batched(nsli, torch, args.batched, args.steps, max(3, args.warmup))
+        if rank == 0:
+            print(json.dumps({"metric": "batched ModAP iterations/sec", "value": r["problem_iterations_per_s"],
+                              "unit": "problem-iterations/s", "config": {"workload": args.batched}, **r}),
+                  flush=True)
+        return 0
     w = WORKLOADS[args.workload]
     m, n = w["m"], w["n"]
     t_gen = time.perf_counter()
@@ -325,6 +376,9 @@ def main():
                         "map_gbs": vb / (r["map_ms_avg"] / 1000.0) / 1e9,
                         "map_frac_of_measured_hbm": vb / (r["map_ms_avg"] / 1000.0) / 1e9 / peak,
                         "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
+
+    if args.batched:
+        variants["batched_bf16"] = time_batched(nsli, torch, args.batched, min(K, 100), W)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -61,11 +62,13 @@ struct State {
 };
 
 struct EpiArgs {
-    int mode;          // 0: GEMM 1 epilogue, 1: GEMM 2 step, 2: GEMM 2 writing y only
+    int mode;          // 0: GEMM 1 epilogue, 3: GEMM 2 partial sums of one K split
     int Pp, nprob, BN;
     long long Mdim;    // rows of the A operand (m, or n for GEMM 2)
-    int ktiles;        // K / 64, rounded up
-    int mtiles;
+    int ktiles;        // 64-wide K chunks per K split
+    int ktiles_total;  // 64-wide K chunks of the whole contraction
+    int mtiles;        // 128-row tiles of the A operand
+    int nwork;         // mtiles * K splits
     // GEMM 1
     const float *b0f, *avf, *invn2f;
     const long long *s_off;
@@ -77,7 +80,7 @@ struct EpiArgs {
     double *X64;              // [Pp][ldx]
     __nv_bfloat16 *Xs;        // [3 Pp][ldx]
     long long ldx;
-    double *Yout;             // [Pp][ldx] (mode 2)
+    float *Ypart;             // [splits][Pp][ldx] (mode 3)
     State *st;
 };
 
@@ -251,8 +254,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0;
             unsigned int ph = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < e.mtiles && ok; tile += gridDim.x) {
-                for (int kc = 0; kc < e.ktiles; ++kc) {
+            for (int w = blockIdx.x; w < e.nwork && ok; w += gridDim.x) {
+                const int tile = w % e.mtiles, ks = w / e.mtiles;
+                const int kbeg = ks * e.ktiles;
+                const int kend = min(kbeg + e.ktiles, e.ktiles_total);
+                for (int kc = kbeg; kc < kend; ++kc) {
                     if (!wait_bar(smem_u32(&bars[4 + s]), ph ^ 1u, abort)) {
                         ok = false;
                         break;
@@ -288,12 +294,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             int acc = 0;
             unsigned int aph = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < e.mtiles && ok; tile += gridDim.x) {
+            for (int w = blockIdx.x; w < e.nwork && ok; w += gridDim.x) {
+                const int ks = w / e.mtiles;
+                const int kbeg = ks * e.ktiles;
+                const int kend = min(kbeg + e.ktiles, e.ktiles_total);
                 if (!wait_bar(smem_u32(&bars[10 + acc]), aph ^ 1u, abort))
                     break;
                 tc_fence_after();
                 const unsigned int dcol = tmem_base + (unsigned int)(acc * kAccCols);
-                for (int kc = 0; kc < e.ktiles; ++kc) {
+                for (int kc = kbeg; kc < kend; ++kc) {
                     if (!wait_bar(smem_u32(&bars[s]), ph, abort)) {
                         ok = false;
                         break;
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int k16 = 0; k16 < BK / 16; ++k16) {
                         const unsigned long long ad = sdesc(sa + k16 * 32);
                         const unsigned long long bd = sdesc(sa + kStageA + k16 * 32);
-                        mma_bf16(dcol, ad, bd, idesc, (kc > 0 || k16 > 0) ? 1u : 0u);
+                        mma_bf16(dcol, ad, bd, idesc, (kc > kbeg || k16 > 0) ? 1u : 0u);
                     }
                     mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
                     if (++s == NSTAGE) {
@@ -330,8 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long k = e.st->k;
         const int cur = (int)(k & 1);
         const float rho = (float)e.st->rho;
-        const double lam = e.st->lambda;
-        for (int tile = blockIdx.x; tile < e.mtiles; tile += gridDim.x) {
+        for (int w = blockIdx.x; w < e.nwork; w += gridDim.x) {
+            const int tile = w % e.mtiles, ks = w / e.mtiles;
             if (!wait_bar(smem_u32(&bars[8 + acc]), aph, abort))
                 break;
             tc_fence_after();
@@ -381,6 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             } else {
+                // GEMM 2: the three split columns of each problem, summed, are
+                // this K split's partial y; the finish kernel adds the splits
                 for (int pc = 0; pc < e.Pp; pc += 16) {
                     float v0[16], v1[16], v2[16];
                     tmem_ld16(tbase + pc, v0);
@@ -390,23 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int p = pc + q;
-                        if (valid && p < e.nprob) {
-                            const double y = (double)((v0[q] + v1[q]) + v2[q]);
-                            const long long ix = (long long)p * e.ldx + row;
-                            if (e.mode == 2) {
-                                e.Yout[ix] = y;
-                            } else {
-                                const int hc = e.cnt[cur * e.Pp + p];
-                                const double s = hc > 0 ? lam / (double)hc : 0.0;
-                                const double xn = e.X64[ix] - s * y;
-                                e.X64[ix] = xn;
-                                __nv_bfloat16 h, m, l;
-                                split3((float)xn, h, m, l);
-                                e.Xs[ix] = h;
-                                e.Xs[(long long)e.Pp * e.ldx + ix] = m;
-                                e.Xs[(long long)(2 * e.Pp) * e.ldx + ix] = l;
-                            }
-                        }
+                        if (valid && p < e.nprob)
+                            e.Ypart[((long long)ks * e.Pp + p) * e.ldx + row] = (v0[q] + v1[q]) + v2[q];
                     }
                 }
             }
@@ -432,6 +428,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------ helper kernels ----
+
+// y_p[j] = sum over K splits (in order) of the partials; then either the
+// relaxed step of problem p (mode 1) or y written out (mode 2).
+__global__ void finish_kernel(const float *Ypart, int splits, int Pp, int nprob, long long n, long long ldx,
+                              const int *cnt, const State *st, double *X64, __nv_bfloat16 *Xs, double *Yout,
+                              int mode)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nprob * ldx)
+        return;
+    const long long p = t / ldx, j = t % ldx;
+    if (j >= n)
+        return;
+    double y = 0.0;
+    for (int ks = 0; ks < splits; ++ks)
+        y += (double)Ypart[((long long)ks * Pp + p) * ldx + j];
+    const long long ix = p * ldx + j;
+    if (mode == 2) {
+        Yout[ix] = y;
+        return;
+    }
+    const int cur = (int)(st->k & 1);
+    const int hc = cnt[cur * Pp + p];
+    const double s = hc > 0 ? st->lambda / (double)hc : 0.0;
+    const double xn = X64[ix] - s * y;
+    X64[ix] = xn;
+    __nv_bfloat16 h, m, l;
+    split3((float)xn, h, m, l);
+    Xs[ix] = h;
+    Xs[(long long)Pp * ldx + ix] = m;
+    Xs[(long long)(2 * Pp) * ldx + ix] = l;
+}
 
 // AT[j][i] = A[i][j] (bf16), 32 x 32 tiles through shared memory.
 __global__ void transpose_kernel(const __nv_bfloat16 *A, long long lda, __nv_bfloat16 *AT, long long ldt, long long m,
@@ -527,6 +555,8 @@ struct nsli_batch_solver {
     int nprob = 0, Pp = 0, BN = 0, num_sms = 1;
     __nv_bfloat16 *A = nullptr, *AT = nullptr, *Xs = nullptr, *Ws = nullptr;
     double *b0_64 = nullptr, *av_64 = nullptr, *n2_64 = nullptr, *X64 = nullptr, *Y = nullptr;
+    float *Ypart = nullptr;
+    int splits = 1, split_tiles = 1;
     float *b0f = nullptr, *avf = nullptr, *invn2f = nullptr;
     long long *s_off = nullptr;
     int *cnt = nullptr, *flags = nullptr;
@@ -593,7 +623,7 @@ void bfree(nsli_batch h)
 {
     if (h->graph)
         cudaGraphExecDestroy(h->graph);
-    void *p[] = {h->A, h->AT, h->Xs, h->Ws, h->b0_64, h->av_64, h->n2_64, h->X64, h->Y, h->b0f, h->avf,
+    void *p[] = {h->A, h->AT, h->Xs, h->Ws, h->b0_64, h->av_64, h->n2_64, h->X64, h->Y, h->Ypart, h->b0f, h->avf,
                  h->invn2f, h->s_off, h->cnt, h->flags, h->maxv, h->st, h->vst, h->ver};
     for (void *q : p)
         if (q)
@@ -621,28 +651,41 @@ EpiArgs epi_args(nsli_batch h, int mode)
     e.X64 = h->X64;
     e.Xs = h->Xs;
     e.ldx = h->ldn;
-    e.Yout = h->Y;
+    e.Ypart = h->Ypart;
     e.st = h->st;
     if (mode == 0) {
         e.Mdim = h->m;
-        e.ktiles = (int)((h->n + BK - 1) / BK);
+        e.ktiles_total = (int)((h->n + BK - 1) / BK);
+        e.ktiles = e.ktiles_total;
         e.mtiles = (int)((h->m + BM - 1) / BM);
+        e.nwork = e.mtiles;
     } else {
         e.Mdim = h->n;
-        e.ktiles = (int)((h->m + BK - 1) / BK);
+        e.ktiles_total = (int)((h->m + BK - 1) / BK);
+        e.ktiles = h->split_tiles;
         e.mtiles = (int)((h->n + BM - 1) / BM);
+        e.nwork = e.mtiles * h->splits;
     }
     return e;
 }
 
+// mode 0: GEMM 1 with its epilogue; mode 1 / 2: GEMM 2 partial sums, then
+// the finish kernel (1: relaxed step, 2: y written out)
 cudaError_t launch_gemm(nsli_batch h, int mode)
 {
-    const EpiArgs e = epi_args(h, mode);
-    const int grid = std::min(h->num_sms, e.mtiles);
-    if (mode == 0)
+    const EpiArgs e = epi_args(h, mode == 0 ? 0 : 3);
+    const int grid = std::min(h->num_sms, e.nwork);
+    if (mode == 0) {
         gemm_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(h->tmA, h->tmX, e);
-    else
-        gemm_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(h->tmAT, h->tmW, e);
+        return cudaGetLastError();
+    }
+    gemm_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(h->tmAT, h->tmW, e);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess)
+        return err;
+    const long long tot = (long long)h->nprob * h->ldn;
+    finish_kernel<<<(unsigned int)((tot + 255) / 256), 256, 0, h->stream>>>(
+        h->Ypart, h->splits, h->Pp, h->nprob, h->n, h->ldn, h->cnt, h->st, h->X64, h->Xs, h->Y, mode);
     return cudaGetLastError();
 }
 
@@ -719,6 +762,22 @@ int nsli_batch_create(nsli_batch *out, int64_t m, int64_t n, int32_t nprob, cons
     BCKC(cudaMalloc((void **)&h->Ws, (size_t)3 * h->Pp * h->ldm * 2), "allocate W splits");
     BCKC(cudaMalloc((void **)&h->X64, (size_t)h->Pp * h->ldn * 8), "allocate X");
     BCKC(cudaMalloc((void **)&h->Y, (size_t)h->Pp * h->ldn * 8), "allocate Y");
+    {
+        // K splits of GEMM 2 so that its (n / 128) x splits work items fill the SMs
+        const long long jt = (n + BM - 1) / BM;
+        const long long kt = (m + BK - 1) / BK;
+        h->splits = (int)std::max<long long>(1, std::min<long long>(h->num_sms / std::max<long long>(1, jt), kt));
+        if (const char *env = std::getenv("NSLI_BATCH_SPLITS")) {
+            const int v = std::atoi(env);
+            if (v >= 1 && v <= 64)
+                h->splits = (int)std::min<long long>(v, kt);
+        }
+        // equal chunk counts per split and no empty split
+        const long long per = (kt + h->splits - 1) / h->splits;
+        h->splits = (int)((kt + per - 1) / per);
+        h->split_tiles = (int)per;
+    }
+    BCKC(cudaMalloc((void **)&h->Ypart, (size_t)h->splits * h->Pp * h->ldn * 4), "allocate partial y");
     BCKC(cudaMalloc((void **)&h->b0_64, (size_t)m * 8), "allocate b0");
     BCKC(cudaMalloc((void **)&h->av_64, (size_t)m * 8), "allocate Av");
     BCKC(cudaMalloc((void **)&h->n2_64, (size_t)m * 8), "allocate norms");
@@ -865,11 +924,11 @@ int nsli_batch_iterate(nsli_batch h, const nsli_params *p, int64_t n_iter)
     }
     for (long long i = 0; i < full; ++i) {
         BCK(cudaGraphLaunch(h->graph, h->stream), "launch batch graph");
-        h->launches += 3ll * B;
+        h->launches += 4ll * B;
     }
     for (long long i = 0; i < rem; ++i) {
         BCK(launch_batch_iteration(h), "launch batch iteration");
-        h->launches += 3;
+        h->launches += 4;
     }
     return NSLI_OK;
 }
@@ -881,7 +940,7 @@ int nsli_batch_map_reduce(nsli_batch h, double rho, double *Y, int64_t *violated
     BCK(cudaMemcpyAsync(&h->st->rho, &rho, 8, cudaMemcpyHostToDevice, h->stream), "set rho");
     BCK(launch_gemm(h, 0), "launch GEMM 1");
     BCK(launch_gemm(h, 2), "launch GEMM 2");
-    h->launches += 2;
+    h->launches += 3;
     int rc = read_error(h);
     if (rc != NSLI_OK)
         return rc;
