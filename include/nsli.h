@@ -247,6 +247,57 @@ int nsli_batch_sync(nsli_batch h);
 void nsli_batch_destroy(nsli_batch h);
 const char *nsli_batch_last_error(nsli_batch h);
 
+/* ---- Pool: continuous batching of many problems of mixed sizes ----------
+ * Problems are admitted while they fit (the pool's byte budget and the
+ * device's free memory), stay resident with their A, x and b across ticks,
+ * and advance together: one round = ONE grouped Map launch over the row
+ * blocks of every live problem + ONE grouped reduce-and-step launch.  Each
+ * problem's row blocks and thread mapping depend only on itself, so its
+ * iterates are bit-identical alone and in any mix.  Finished problems stop
+ * costing work at once (their blocks return) and keep their x until
+ * removed.  The paper's master-slave farm (Section 3) runs one problem; the
+ * pool is this build's serving form of the same iteration. */
+typedef struct nsli_pool_s *nsli_pool;
+
+/* storage: NSLI_BF16 or NSLI_F32.  max_bytes: device-memory budget of the
+ * pool (0: only free HBM limits admission).  stream as in nsli_create. */
+int nsli_pool_create(nsli_pool *out, int32_t storage, int64_t max_bytes, void *stream);
+
+/* Admit one problem (arguments as nsli_create with a binary32 A, norms
+ * computed on the device) with its run parameters p (stop rule, eps,
+ * max_iter, lambda, rule, rho).  *slot receives its id.  NSLI_ERR_OOM when
+ * it does not fit: nothing is allocated and the pool is unchanged. */
+int nsli_pool_add(nsli_pool pool, int64_t m, int64_t n, const float *A, int64_t lda,
+                  const double *b0, const double *Av, const double *x0,
+                  const nsli_params *p, int64_t *slot);
+
+/* `rounds` iterations of every live problem (asynchronous). */
+int nsli_pool_step(nsli_pool pool, int32_t rounds);
+
+/* Wall-clock ticks: set tick k of the listed problems (slots/ticks: host
+ * arrays of count entries); from then on their ticks change only here. */
+int nsli_pool_set_ticks(nsli_pool pool, const int64_t *slots, const int64_t *ticks, int64_t count);
+
+/* Synchronise, confirm binary32 stop candidates in binary64 (a rejected one
+ * resumes with a forced step), and report every finished problem (status
+ * NSLI_OK, NSLI_NOT_CONVERGED or an error) in slots/status/iters (host
+ * arrays of cap entries); *count = number of finished problems (may exceed
+ * cap). */
+int nsli_pool_poll(nsli_pool pool, int64_t *slots, int32_t *status, int64_t *iters,
+                   int64_t cap, int64_t *count);
+
+int nsli_pool_get_x(nsli_pool pool, int64_t slot, double *x);
+int nsli_pool_residual_max(nsli_pool pool, int64_t slot, double *max_viol,
+                           double *max_viol_norm);
+/* Release a problem's device memory (its slot id becomes free). */
+int nsli_pool_remove(nsli_pool pool, int64_t slot);
+int64_t nsli_pool_live(nsli_pool pool);
+int64_t nsli_pool_bytes_used(nsli_pool pool);
+int64_t nsli_pool_launch_count(nsli_pool pool);
+int nsli_pool_sync(nsli_pool pool);
+void nsli_pool_destroy(nsli_pool pool);
+const char *nsli_pool_last_error(nsli_pool pool);
+
 /* Number of kernels the handle has launched so far (graph nodes included). */
 int64_t nsli_launch_count(nsli_handle h);
 

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "nsli.h"
 #include "nsli_internal.h"
@@ -809,5 +810,411 @@ int nsli_get_result(nsli_handle h, nsli_result *out)
     *out = r;
     return NSLI_OK;
 }
+
+}  // extern "C"
+
+// ============================================================== pool ======
+//
+// Continuous batching of many problems: each problem is an nsli_solver
+// (its own device buffers, state and ring configuration); a round is one
+// grouped Map launch over the work items of every live problem and one
+// grouped reduce-and-step launch.  A problem's items (row blocks) and
+// thread mapping depend only on that problem, so its iterates are the same
+// alone and in any mix.
+
+struct nsli_pool_s {
+    int storage = NSLI_BF16;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 1;
+    long long max_bytes = 0, used_bytes = 0;
+    std::vector<nsli_solver *> slots;       // slot id -> problem (nullptr when free)
+    std::vector<long long> slot_bytes;
+    std::vector<int> slot_items;
+    bool dirty = true;
+    int n_items = 0, n_red = 0, n_live = 0;
+    size_t smem = 0;
+    GroupProblem *d_probs = nullptr;
+    GroupItem *d_items = nullptr;
+    GroupRed *d_red = nullptr;
+    size_t cap_probs = 0, cap_items = 0, cap_red = 0;
+    DevState **d_sts = nullptr;
+    long long *d_ticks = nullptr;
+    size_t cap_ticks = 0;
+    DevState *h_states = nullptr;            // pinned mirror for polling
+    size_t cap_states = 0;
+    std::vector<int> live_order;             // slot ids in the current tables
+    long long launches = 0;
+    std::string last_error;
+};
+
+namespace {
+
+int perr(nsli_pool p, int code, const std::string &msg)
+{
+    if (p)
+        p->last_error = msg;
+    return code;
+}
+#define PCK(call, what)                                                                                      \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return perr(p, e_ == cudaErrorMemoryAllocation ? NSLI_ERR_OOM : NSLI_ERR_CUDA,                  \
+                        std::string(what) + ": " + cudaGetErrorString(e_));                                  \
+    } while (0)
+
+// device bytes a problem will take (A, records, vectors, partials)
+long long problem_bytes(int storage, long long m, long long n, int num_sms)
+{
+    const int eb = storage == NSLI_F64 ? 8 : storage == NSLI_F32 ? 4 : storage == NSLI_BF16 ? 2 : 1;
+    const long long ld = n + 16;
+    const long long G = std::min<long long>(num_sms, m);
+    return m * ld * eb + m * (32 + 3 * 8 + 4) + G * ld * 8 + ld * 40 + (1 << 16);
+}
+
+int items_of(nsli_solver *h)
+{
+    // about 1 MiB of A per item, at most one item per Map CTA of the handle
+    const long long bytes = h->m * (long long)h->row_bytes;
+    const long long want = (bytes + (1ll << 20) - 1) >> 20;
+    return (int)std::max<long long>(1, std::min<long long>(want, h->G));
+}
+
+template <typename T> int grow(nsli_pool p, T **buf, size_t *cap, size_t need)
+{
+    if (*cap >= need)
+        return NSLI_OK;
+    size_t c = std::max<size_t>(need, *cap * 2 + 16);
+    if (*buf)
+        cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    PCK(cudaMalloc((void **)buf, c * sizeof(T)), "grow pool table");
+    *cap = c;
+    return NSLI_OK;
+}
+
+int rebuild_tables(nsli_pool p)
+{
+    std::vector<GroupProblem> probs;
+    std::vector<GroupItem> items;
+    std::vector<GroupRed> reds;
+    p->live_order.clear();
+    size_t smem = kSmemHeader;
+    for (size_t sid = 0; sid < p->slots.size(); ++sid) {
+        nsli_solver *h = p->slots[sid];
+        if (!h)
+            continue;
+        const int pi = (int)probs.size();
+        const int nitems = p->slot_items[sid];
+        GroupProblem gp;
+        gp.map = map_args(h);
+        gp.red = reduce_args(h);
+        gp.red.G = nitems;
+        gp.nt = h->consumers;
+        gp.vpt = h->vpt;
+        gp.red_blocks = h->red_grid;
+        gp.first_red = (int)reds.size();
+        probs.push_back(gp);
+        const long long base = h->m / nitems, rem = h->m % nitems;
+        long long r = 0;
+        for (int q = 0; q < nitems; ++q) {
+            const long long cnt = base + (q < rem ? 1 : 0);
+            items.push_back(GroupItem{pi, q, r, r + cnt});
+            r += cnt;
+        }
+        for (int b = 0; b < h->red_grid; ++b)
+            reds.push_back(GroupRed{pi, b});
+        smem = std::max(smem, h->smem);
+        p->live_order.push_back((int)sid);
+    }
+    int rc;
+    if ((rc = grow(p, &p->d_probs, &p->cap_probs, std::max<size_t>(1, probs.size()))) != NSLI_OK)
+        return rc;
+    if ((rc = grow(p, &p->d_items, &p->cap_items, std::max<size_t>(1, items.size()))) != NSLI_OK)
+        return rc;
+    if ((rc = grow(p, &p->d_red, &p->cap_red, std::max<size_t>(1, reds.size()))) != NSLI_OK)
+        return rc;
+    PCK(cudaStreamSynchronize(p->stream), "synchronize");
+    if (!probs.empty()) {
+        PCK(cudaMemcpy(p->d_probs, probs.data(), probs.size() * sizeof(GroupProblem), cudaMemcpyHostToDevice),
+            "upload problems");
+        PCK(cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(GroupItem), cudaMemcpyHostToDevice),
+            "upload items");
+        PCK(cudaMemcpy(p->d_red, reds.data(), reds.size() * sizeof(GroupRed), cudaMemcpyHostToDevice),
+            "upload reduce table");
+    }
+    if (smem > p->smem) {
+        PCK(map_group_prepare(p->storage, smem), "configure grouped Map");
+        p->smem = smem;
+    }
+    p->n_items = (int)items.size();
+    p->n_red = (int)reds.size();
+    p->n_live = (int)probs.size();
+    p->dirty = false;
+    return NSLI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nsli_pool_create(nsli_pool *out, int32_t storage, int64_t max_bytes, void *stream)
+{
+    if (!out || (storage != NSLI_BF16 && storage != NSLI_F32) || max_bytes < 0)
+        return NSLI_ERR_ARG;
+    *out = nullptr;
+    nsli_pool p = new nsli_pool_s();
+    p->storage = storage;
+    p->max_bytes = max_bytes;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete p;
+        return NSLI_ERR_CUDA;
+    }
+    if (stream) {
+        p->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete p;
+            return NSLI_ERR_CUDA;
+        }
+        p->own_stream = true;
+    }
+    *out = p;
+    return NSLI_OK;
+}
+
+void nsli_pool_destroy(nsli_pool p)
+{
+    if (!p)
+        return;
+    cudaStreamSynchronize(p->stream);
+    for (nsli_solver *h : p->slots)
+        if (h) {
+            h->stream = nullptr;  // the pool's stream is not the handle's to destroy
+            h->own_stream = false;
+            free_all(h);
+            delete h;
+        }
+    void *bufs[] = {p->d_probs, p->d_items, p->d_red, p->d_sts, p->d_ticks};
+    for (void *b : bufs)
+        if (b)
+            cudaFree(b);
+    if (p->h_states)
+        cudaFreeHost(p->h_states);
+    if (p->own_stream)
+        cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+int nsli_pool_add(nsli_pool p, int64_t m, int64_t n, const float *A, int64_t lda, const double *b0,
+                  const double *Av, const double *x0, const nsli_params *prm, int64_t *slot)
+{
+    if (!p || !slot || !prm)
+        return NSLI_ERR_ARG;
+    if (m < 1 || n < 1 || lda < n || !A || !b0 || !x0)
+        return perr(p, NSLI_ERR_ARG, "bad problem arguments");
+    // admission by memory: the pool's budget and the device's free HBM
+    const long long need = problem_bytes(p->storage, m, n, p->num_sms);
+    if (p->max_bytes > 0 && p->used_bytes + need > p->max_bytes)
+        return perr(p, NSLI_ERR_OOM, "problem does not fit the pool's memory budget");
+    size_t freeb = 0, totalb = 0;
+    PCK(cudaMemGetInfo(&freeb, &totalb), "query free memory");
+    if ((long long)freeb < need + (256ll << 20))
+        return perr(p, NSLI_ERR_OOM, "problem does not fit the free device memory");
+    nsli_handle h = nullptr;
+    int rc = nsli_create(&h, m, n, p->storage, NSLI_F32, A, lda, b0, nullptr, Av, x0, p->stream);
+    if (rc != NSLI_OK)
+        return perr(p, rc, "create problem");
+    // control state of the problem's run
+    if ((rc = validate_params(h, prm)) != NSLI_OK || (rc = begin_run(h, prm, prm->stop, prm->max_iter)) != NSLI_OK) {
+        h->stream = nullptr;
+        free_all(h);
+        delete h;
+        return perr(p, rc, "problem parameters");
+    }
+    size_t sid = 0;
+    while (sid < p->slots.size() && p->slots[sid])
+        ++sid;
+    if (sid == p->slots.size()) {
+        p->slots.push_back(nullptr);
+        p->slot_bytes.push_back(0);
+        p->slot_items.push_back(0);
+    }
+    p->slots[sid] = h;
+    p->slot_bytes[sid] = need;
+    p->slot_items[sid] = items_of(h);
+    p->used_bytes += need;
+    p->launches += h->launches;
+    p->dirty = true;
+    *slot = (int64_t)sid;
+    return NSLI_OK;
+}
+
+int nsli_pool_remove(nsli_pool p, int64_t slot)
+{
+    if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
+        return NSLI_ERR_ARG;
+    PCK(cudaStreamSynchronize(p->stream), "synchronize");
+    nsli_solver *h = p->slots[slot];
+    h->stream = nullptr;
+    h->own_stream = false;
+    free_all(h);
+    delete h;
+    p->slots[slot] = nullptr;
+    p->used_bytes -= p->slot_bytes[slot];
+    p->dirty = true;
+    return NSLI_OK;
+}
+
+int nsli_pool_step(nsli_pool p, int32_t rounds)
+{
+    if (!p || rounds < 0)
+        return NSLI_ERR_ARG;
+    if (p->dirty) {
+        int rc = rebuild_tables(p);
+        if (rc != NSLI_OK)
+            return rc;
+    }
+    if (p->n_live == 0)
+        return NSLI_OK;
+    const bool f64 = p->storage == NSLI_F64;
+    for (int r = 0; r < rounds; ++r) {
+        PCK(map_group_launch(p->storage, p->n_items, p->smem, p->stream, p->d_probs, p->d_items), "grouped Map");
+        PCK(reduce_group_launch(f64, p->n_red, p->stream, p->d_probs, p->d_red), "grouped reduce");
+        p->launches += 2;
+    }
+    return NSLI_OK;
+}
+
+int nsli_pool_set_ticks(nsli_pool p, const int64_t *slots, const int64_t *ticks, int64_t count)
+{
+    if (!p || count < 0 || (count > 0 && (!slots || !ticks)))
+        return NSLI_ERR_ARG;
+    if (count == 0)
+        return NSLI_OK;
+    std::vector<DevState *> sts((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        if (slots[i] < 0 || slots[i] >= (int64_t)p->slots.size() || !p->slots[slots[i]])
+            return perr(p, NSLI_ERR_ARG, "no problem in that slot");
+        sts[i] = p->slots[slots[i]]->st;
+    }
+    int rc;
+    size_t cap_sts = p->cap_ticks, cap_vals = p->cap_ticks;
+    if ((rc = grow(p, &p->d_sts, &cap_sts, (size_t)count)) != NSLI_OK)
+        return rc;
+    if ((rc = grow(p, &p->d_ticks, &cap_vals, (size_t)count)) != NSLI_OK)
+        return rc;
+    p->cap_ticks = std::min(cap_sts, cap_vals);
+    PCK(cudaStreamSynchronize(p->stream), "synchronize");
+    PCK(cudaMemcpy(p->d_sts, sts.data(), (size_t)count * sizeof(DevState *), cudaMemcpyHostToDevice), "upload states");
+    PCK(cudaMemcpy(p->d_ticks, ticks, (size_t)count * 8, cudaMemcpyHostToDevice), "upload ticks");
+    PCK(set_ticks_launch(p->stream, p->d_sts, p->d_ticks, (int)count), "set ticks");
+    p->launches += 1;
+    return NSLI_OK;
+}
+
+int nsli_pool_poll(nsli_pool p, int64_t *slots, int32_t *status, int64_t *iters, int64_t cap, int64_t *count)
+{
+    if (!p || !count || cap < 0 || (cap > 0 && (!slots || !status || !iters)))
+        return NSLI_ERR_ARG;
+    *count = 0;
+    const size_t ns = p->slots.size();
+    if (p->cap_states < ns) {
+        if (p->h_states)
+            cudaFreeHost(p->h_states);
+        p->h_states = nullptr;
+        PCK(cudaMallocHost((void **)&p->h_states, std::max<size_t>(ns, 16) * sizeof(DevState)), "pinned states");
+        p->cap_states = std::max<size_t>(ns, 16);
+    }
+    for (size_t sid = 0; sid < ns; ++sid)
+        if (p->slots[sid])
+            PCK(cudaMemcpyAsync(&p->h_states[sid], p->slots[sid]->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                p->stream),
+                "read state");
+    PCK(cudaStreamSynchronize(p->stream), "synchronize");
+    for (size_t sid = 0; sid < ns; ++sid) {
+        nsli_solver *h = p->slots[sid];
+        if (!h)
+            continue;
+        DevState &s = p->h_states[sid];
+        int st = s.status;
+        if (s.error & ERRF_TIMEOUT)
+            st = NSLI_ERR_TIMEOUT;
+        if (st == ST_CANDIDATE) {
+            p->launches += 1;
+            int rc = run_verify(h);
+            if (rc != NSLI_OK)
+                return perr(p, rc, "binary64 check");
+            bool accept;
+            if (s.stop == NSLI_STOP_EPSMEM)
+                accept = h->last_check.max_viol_norm < s.eps;
+            else if (s.stop == NSLI_STOP_MAXVIOL_REL)
+                accept = h->last_check.max_viol <= s.eps * h->last_check.max_abs_b;
+            else
+                accept = h->last_check.h == 0;
+            if (accept) {
+                st = NSLI_OK;
+                const int ok = NSLI_OK;  // record the confirmed stop on the device
+                PCK(cudaMemcpyAsync(&h->st->status, &ok, sizeof ok, cudaMemcpyHostToDevice, p->stream),
+                    "record status");
+            } else {
+                PCK(state_resume_launch(p->stream, h->st), "resume");
+                p->launches += 1;
+                continue;
+            }
+        }
+        if (st == ST_RUNNING)
+            continue;
+        if (*count < cap) {
+            slots[*count] = (int64_t)sid;
+            status[*count] = st;
+            iters[*count] = s.it;
+        }
+        ++*count;
+    }
+    return NSLI_OK;
+}
+
+int nsli_pool_get_x(nsli_pool p, int64_t slot, double *x)
+{
+    if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
+        return NSLI_ERR_ARG;
+    return nsli_get_x(p->slots[slot], x);
+}
+
+int nsli_pool_residual_max(nsli_pool p, int64_t slot, double *max_viol, double *max_viol_norm)
+{
+    if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
+        return NSLI_ERR_ARG;
+    return nsli_residual_max(p->slots[slot], max_viol, max_viol_norm);
+}
+
+int64_t nsli_pool_live(nsli_pool p)
+{
+    if (!p)
+        return 0;
+    int64_t c = 0;
+    for (nsli_solver *h : p->slots)
+        c += h ? 1 : 0;
+    return c;
+}
+
+int64_t nsli_pool_bytes_used(nsli_pool p) { return p ? (int64_t)p->used_bytes : 0; }
+
+int64_t nsli_pool_launch_count(nsli_pool p) { return p ? (int64_t)p->launches : 0; }
+
+int nsli_pool_sync(nsli_pool p)
+{
+    if (!p)
+        return NSLI_ERR_ARG;
+    PCK(cudaStreamSynchronize(p->stream), "synchronize");
+    return NSLI_OK;
+}
+
+const char *nsli_pool_last_error(nsli_pool p) { return p ? p->last_error.c_str() : ""; }
 
 }  // extern "C"

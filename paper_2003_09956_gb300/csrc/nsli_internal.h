@@ -40,7 +40,8 @@ struct DevState {
     // control, written by the host before a run
     double lambda, eps, rho;
     long long max_iter;   // absolute bound on `it`
-    int rule, stop, force_step, pad0;
+    int rule, stop, force_step;
+    int hold_tick;        // 1: ticks are set from outside (wall clock), not per iteration
     // progress, written by the kernels
     long long it;         // x-updates performed in this run
     long long tick;       // k of b(k)
@@ -93,6 +94,25 @@ struct ReduceArgs {
     int G;
 };
 
+// Grouped launches (continuous batching): per-problem launch parameters and
+// work items.  A problem's items and thread mapping depend only on itself.
+struct GroupProblem {
+    MapArgs map;        // rows_base / rows_rem unused; part_y has one row per item
+    ReduceArgs red;     // G = number of items of the problem
+    int nt, vpt;        // Map threads owning vectors, vectors per thread
+    int red_blocks;     // reduce blocks of this problem
+    int first_red;      // index of its first block in the grouped reduce launch
+};
+struct GroupItem {
+    int prob;           // index into the GroupProblem array
+    int part;           // index of the item within its problem
+    long long row_begin, row_end;
+};
+struct GroupRed {
+    int prob;
+    int blk;            // block index within the problem
+};
+
 struct VerifyArgs {
     const void *A;
     const double *x64;
@@ -123,6 +143,12 @@ cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &
 cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a,
                                double *y_out);
 cudaError_t verify_launch(int storage, int grid, cudaStream_t s, const VerifyArgs &a);
+// grouped launches over the problems of a pool (one storage type)
+cudaError_t map_group_prepare(int storage, size_t smem);
+cudaError_t map_group_launch(int storage, int items, size_t smem, cudaStream_t s, const GroupProblem *probs,
+                             const GroupItem *it);
+cudaError_t reduce_group_launch(bool f64, int blocks, cudaStream_t s, const GroupProblem *probs,
+                                const GroupRed *tab);
 
 struct PrepArgs {
     const void *src;        // staged source rows (device), row pitch lda
@@ -162,6 +188,8 @@ struct StateBegin {
 };
 cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b);
 cudaError_t state_resume_launch(cudaStream_t s, DevState *st);
+// sts[i]->tick = ticks[i] and ticks held (device arrays of count entries)
+cudaError_t set_ticks_launch(cudaStream_t s, DevState *const *sts, const long long *ticks, int count);
 cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
                                long long n, long long row0, long long rows, double *out);
 

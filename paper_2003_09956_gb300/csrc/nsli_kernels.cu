@@ -253,8 +253,14 @@ template <int RG, typename T> __device__ __forceinline__ T warp_fold_rows(const 
     }
 }
 
+// The Map of rows [row_begin, row_end) of one problem by the calling CTA:
+// the CTA-level sum of the positive slices goes to part_row (ld elements of
+// the accumulation type), the CTA's counters to *stat_out.  Threads
+// t < nt own vectors t + v * nt (v < vpt_used <= VPT); the others only take
+// part in the barriers and reductions (with zero partial sums).
 template <int S, int VPT, bool GUARD>
-__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs p)
+__device__ __forceinline__ void map_body(const MapArgs &p, const long long row_begin, const long long row_end,
+                                         void *part_row, PartStat *stat_out, const int nt, const int vpt_used)
 {
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
@@ -265,8 +271,6 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     constexpr int NCH = (VPT >= 4 && RG <= 2) ? 2 : 1;  // independent chains per row
 
     DevState *st = p.st;
-    if (!p.ignore_done && *(volatile int *)&st->done)
-        return;
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);  // full[8], empty[8]
@@ -274,13 +278,9 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     unsigned char *stages = smem + kSmemHeader;
 
     const int tid = threadIdx.x;
-    const int nt = (int)blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int nwarps = nt >> 5;
+    const int nwarps = (int)blockDim.x >> 5;
 
-    const long long b = blockIdx.x;
-    const long long row_begin = b * p.rows_base + (b < p.rows_rem ? b : (long long)p.rows_rem);
-    const long long row_end = row_begin + p.rows_base + (b < p.rows_rem ? 1 : 0);
     const int R = p.rows_per_slot;
     const int nslots = (int)((row_end - row_begin + R - 1) / R);
     const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     for (int v = 0; v < VPT; ++v) {
         const int j = tid + v * nt;
         voff[v] = j * 16;
-        vok[v] = !GUARD || j < p.nv;
+        vok[v] = v < vpt_used && tid < nt && (!GUARD || j < p.nv);
     }
 
     Acc xr[VPT][EPV];
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
             const Acc wsum = warp_fold_rows<RG>(acc, lane);
             if ((lane & (W - 1)) == 0)
                 rb[(lane / W) * 32 + warp] = wsum;
-            aborted = bar_all_or(nt, timed_out);
+            aborted = bar_all_or((int)blockDim.x, timed_out);  // every thread of the block arrives
             if (aborted)
                 break;
             if (tid == 0 && g0 == 0 && s >= 1 && issued < nslots) {
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
         return;
     }
 
-    Acc *py = static_cast<Acc *>(p.part_y) + (long long)blockIdx.x * p.ld;
+    Acc *py = static_cast<Acc *>(part_row);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
         if (vok[v]) {
@@ -493,8 +493,39 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
         ps.maxviol = (double)mv;
         ps.maxnorm = (double)mn;
         ps.maxb = (double)mb;
-        p.part_stat[blockIdx.x] = ps;
+        *stat_out = ps;
     }
+}
+
+// One problem: CTA b maps its contiguous balanced block of rows.
+template <int S, int VPT, bool GUARD>
+__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs p)
+{
+    using Acc = typename Traits<S>::acc;
+    if (!p.ignore_done && *(volatile int *)&p.st->done)
+        return;
+    const long long b = blockIdx.x;
+    const long long row_begin = b * p.rows_base + (b < p.rows_rem ? b : (long long)p.rows_rem);
+    const long long row_end = row_begin + p.rows_base + (b < p.rows_rem ? 1 : 0);
+    map_body<S, VPT, GUARD>(p, row_begin, row_end, static_cast<Acc *>(p.part_y) + b * p.ld, p.part_stat + b,
+                            (int)blockDim.x, VPT);
+}
+
+// Many problems in one launch: CTA b maps work item b (a block of rows of
+// one problem) with that problem's own thread mapping, so a problem's
+// partial sums do not depend on which other problems share the launch.
+template <int S, int VPT>
+__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_group_kernel(const GroupProblem *probs,
+                                                                        const GroupItem *items)
+{
+    using Acc = typename Traits<S>::acc;
+    const GroupItem it = items[blockIdx.x];
+    const GroupProblem &gp = probs[it.prob];
+    if (*(volatile int *)&gp.map.st->done)
+        return;
+    map_body<S, VPT, true>(gp.map, it.row_begin, it.row_end,
+                           static_cast<Acc *>(gp.map.part_y) + (long long)it.part * gp.map.ld,
+                           gp.map.part_stat + it.part, gp.nt, gp.vpt);
 }
 
 // ---------------------------------------------------- reduce and update ----
@@ -541,8 +572,9 @@ __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceSh
     }
 }
 
+// Column block `blk` of `nblk` of one problem's reduce-and-step.
 template <typename Acc>
-__global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
+__device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, const int nblk)
 {
     DevState *st = p.st;
     if (*(volatile int *)&st->done)
@@ -562,7 +594,7 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
     const bool step = !pass && !at_max;
     const int rule = st->rule;
     const double lambda = st->lambda;
-    const long long j = (long long)blockIdx.x * kReduceCols + lane;
+    const long long j = (long long)blk * kReduceCols + lane;
 
     if (step) {
         double yj = 0.0;
@@ -596,13 +628,13 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
         }
         val = warp_sum(val);
         if (lane == 0)
-            p.part_dx[blockIdx.x] = val;
+            p.part_dx[blk] = val;
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int t = atomicAdd(&st->ticket, 1u);
-        sh.last = (t == gridDim.x - 1) ? 1 : 0;
+        sh.last = (t == (unsigned int)nblk - 1) ? 1 : 0;
     }
     __syncthreads();
     if (!sh.last)
@@ -613,7 +645,7 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
     if (step) {
         if (grp == 0) {
             double v = 0.0;
-            for (int q = lane; q < (int)gridDim.x; q += 32)
+            for (int q = lane; q < nblk; q += 32)
                 v += __ldcg(p.part_dx + q);
             v = warp_sum(v);
             if (lane == 0)
@@ -660,7 +692,8 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
             st->done = 1;
         } else {
             st->it += 1;
-            st->tick += 1;
+            if (!st->hold_tick)
+                st->tick += 1;
             st->dx_norm = sqrt(dx2);
             st->y_norm = ynorm;
             if (stop == NSLI_STOP_STEP && sqrt(dx2) < eps) {
@@ -671,6 +704,21 @@ __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
         st->force_step = 0;
         st->ticket = 0u;
     }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
+{
+    reduce_body<Acc>(p, blockIdx.x, gridDim.x);
+}
+
+// Many problems in one launch: block b serves (problem, column block) tab[b].
+template <typename Acc>
+__global__ void __launch_bounds__(256) reduce_group_kernel(const GroupProblem *probs, const GroupRed *tab)
+{
+    const GroupRed t = tab[blockIdx.x];
+    const GroupProblem &gp = probs[t.prob];
+    reduce_body<Acc>(gp.red, t.blk, gp.red_blocks);
 }
 
 // Map + Reduce without a step (diagnostics and parity): y in binary64.
@@ -933,6 +981,15 @@ __global__ void state_begin_kernel(DevState *st, const StateBegin b)
     st->ticket = 0u;
 }
 
+__global__ void set_ticks_kernel(DevState *const *sts, const long long *ticks, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        sts[i]->tick = ticks[i];
+        sts[i]->hold_tick = 1;
+    }
+}
+
 __global__ void state_resume_kernel(DevState *st)
 {
     st->done = 0;
@@ -1024,6 +1081,40 @@ cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers
     return cudaLaunchKernel(fn, dim3(grid), dim3(consumers), args, smem, s);
 }
 
+cudaError_t map_group_prepare(int storage, size_t smem)
+{
+    const void *fn = nullptr;
+    if (storage == NSLI_BF16)
+        fn = (const void *)map_group_kernel<NSLI_BF16, 4>;
+    else if (storage == NSLI_F32)
+        fn = (const void *)map_group_kernel<NSLI_F32, 8>;
+    if (!fn)
+        return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t map_group_launch(int storage, int items, size_t smem, cudaStream_t s, const GroupProblem *probs,
+                             const GroupItem *it)
+{
+    if (storage == NSLI_BF16)
+        map_group_kernel<NSLI_BF16, 4><<<items, kMapMaxConsumers, smem, s>>>(probs, it);
+    else if (storage == NSLI_F32)
+        map_group_kernel<NSLI_F32, 8><<<items, kMapMaxConsumers, smem, s>>>(probs, it);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_group_launch(bool f64, int blocks, cudaStream_t s, const GroupProblem *probs,
+                                const GroupRed *tab)
+{
+    if (f64)
+        reduce_group_kernel<double><<<blocks, 256, 0, s>>>(probs, tab);
+    else
+        reduce_group_kernel<float><<<blocks, 256, 0, s>>>(probs, tab);
+    return cudaGetLastError();
+}
+
 cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a)
 {
     if (f64)
@@ -1098,6 +1189,12 @@ cudaError_t check_finite_launch(cudaStream_t s, const double *v, long long n, in
 cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b)
 {
     state_begin_kernel<<<1, 1, 0, s>>>(st, b);
+    return cudaGetLastError();
+}
+
+cudaError_t set_ticks_launch(cudaStream_t s, DevState *const *sts, const long long *ticks, int count)
+{
+    set_ticks_kernel<<<(count + 127) / 128, 128, 0, s>>>(sts, ticks, count);
     return cudaGetLastError();
 }
 

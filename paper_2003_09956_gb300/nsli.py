@@ -68,7 +68,11 @@ EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed",
            "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc",
            "nsli_batch_create", "nsli_batch_iterate", "nsli_batch_map_reduce", "nsli_batch_get_x",
            "nsli_batch_residual_max", "nsli_batch_launch_count", "nsli_batch_sync",
-           "nsli_batch_destroy", "nsli_batch_last_error"]
+           "nsli_batch_destroy", "nsli_batch_last_error",
+           "nsli_pool_create", "nsli_pool_add", "nsli_pool_step", "nsli_pool_set_ticks",
+           "nsli_pool_poll", "nsli_pool_get_x", "nsli_pool_residual_max", "nsli_pool_remove",
+           "nsli_pool_live", "nsli_pool_bytes_used", "nsli_pool_launch_count", "nsli_pool_sync",
+           "nsli_pool_destroy", "nsli_pool_last_error"]
 
 
 def library_path() -> str:
@@ -143,6 +147,32 @@ def load(path: str | None = None):
         lib.nsli_batch_destroy.restype = None
         lib.nsli_batch_last_error.argtypes = [H]
         lib.nsli_batch_last_error.restype = ctypes.c_char_p
+        lib.nsli_pool_create.argtypes = [ctypes.POINTER(H), i32, i64, P]
+        lib.nsli_pool_create.restype = ctypes.c_int
+        lib.nsli_pool_add.argtypes = [H, i64, i64, P, i64, P, P, P, ctypes.POINTER(nsli_params),
+                                      ctypes.POINTER(i64)]
+        lib.nsli_pool_add.restype = ctypes.c_int
+        lib.nsli_pool_step.argtypes = [H, i32]
+        lib.nsli_pool_step.restype = ctypes.c_int
+        lib.nsli_pool_set_ticks.argtypes = [H, P, P, i64]
+        lib.nsli_pool_set_ticks.restype = ctypes.c_int
+        lib.nsli_pool_poll.argtypes = [H, P, P, P, i64, ctypes.POINTER(i64)]
+        lib.nsli_pool_poll.restype = ctypes.c_int
+        lib.nsli_pool_get_x.argtypes = [H, i64, P]
+        lib.nsli_pool_get_x.restype = ctypes.c_int
+        lib.nsli_pool_residual_max.argtypes = [H, i64, ctypes.POINTER(d), ctypes.POINTER(d)]
+        lib.nsli_pool_residual_max.restype = ctypes.c_int
+        lib.nsli_pool_remove.argtypes = [H, i64]
+        lib.nsli_pool_remove.restype = ctypes.c_int
+        for nm in ("nsli_pool_live", "nsli_pool_bytes_used", "nsli_pool_launch_count"):
+            getattr(lib, nm).argtypes = [H]
+            getattr(lib, nm).restype = i64
+        lib.nsli_pool_sync.argtypes = [H]
+        lib.nsli_pool_sync.restype = ctypes.c_int
+        lib.nsli_pool_destroy.argtypes = [H]
+        lib.nsli_pool_destroy.restype = None
+        lib.nsli_pool_last_error.argtypes = [H]
+        lib.nsli_pool_last_error.restype = ctypes.c_char_p
         if path is None:
             _lib = lib
         return lib
@@ -425,3 +455,99 @@ class BatchSolver:
 
     def sync(self):
         self._check(load().nsli_batch_sync(self._h), "nsli_batch_sync")
+
+
+class Pool:
+    """Device-resident problems advanced together (continuous batching).
+    See nsli_pool_* in include/nsli.h."""
+
+    def __init__(self, storage="bf16", max_bytes=0, stream=None):
+        h = ctypes.c_void_p()
+        rc = load().nsli_pool_create(ctypes.byref(h), STORAGE[storage], int(max_bytes),
+                                     None if stream is None else ctypes.c_void_p(stream))
+        if rc != OK:
+            raise NsliError(rc, "nsli_pool_create")
+        self._h = h
+
+    def _check(self, rc, where):
+        if rc < 0:
+            raise NsliError(rc, where, load().nsli_pool_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nsli_pool_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, A, b0, x0, Av=None, **params):
+        """Admit a problem; returns its slot, or None when it does not fit."""
+        m, n = int(A.shape[0]), int(A.shape[1])
+        if isinstance(A, np.ndarray):
+            A = np.ascontiguousarray(A, dtype=np.float32)
+        b0, x0, Av = _f64(b0, m), _f64(x0, n), _f64(Av, m)
+        _sync_torch_inputs(A, b0, x0, Av)
+        p = make_params(**params)
+        slot = ctypes.c_int64(-1)
+        rc = load().nsli_pool_add(self._h, m, n, _ptr(A), n, _ptr(b0), _ptr(Av), _ptr(x0),
+                                  ctypes.byref(p), ctypes.byref(slot))
+        if rc == ERR_OOM:
+            return None
+        self._check(rc, "nsli_pool_add")
+        return int(slot.value)
+
+    def step(self, rounds=1):
+        self._check(load().nsli_pool_step(self._h, int(rounds)), "nsli_pool_step")
+
+    def set_ticks(self, slots, ticks):
+        sl = np.ascontiguousarray(slots, dtype=np.int64)
+        tk = np.ascontiguousarray(ticks, dtype=np.int64)
+        self._check(load().nsli_pool_set_ticks(self._h, _ptr(sl), _ptr(tk), int(sl.size)),
+                    "nsli_pool_set_ticks")
+
+    def poll(self, cap=4096):
+        sl = np.empty(cap, np.int64)
+        st = np.empty(cap, np.int32)
+        it = np.empty(cap, np.int64)
+        cnt = ctypes.c_int64()
+        self._check(load().nsli_pool_poll(self._h, _ptr(sl), _ptr(st), _ptr(it), cap, ctypes.byref(cnt)),
+                    "nsli_pool_poll")
+        k = min(int(cnt.value), cap)
+        return [(int(sl[i]), int(st[i]), int(it[i])) for i in range(k)]
+
+    def get_x(self, slot, n):
+        x = np.empty(n, np.float64)
+        self._check(load().nsli_pool_get_x(self._h, int(slot), _ptr(x)), "nsli_pool_get_x")
+        return x
+
+    def residual_max(self, slot):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(load().nsli_pool_residual_max(self._h, int(slot), ctypes.byref(a), ctypes.byref(b)),
+                    "nsli_pool_residual_max")
+        return a.value, b.value
+
+    def remove(self, slot):
+        self._check(load().nsli_pool_remove(self._h, int(slot)), "nsli_pool_remove")
+
+    def live(self):
+        return int(load().nsli_pool_live(self._h))
+
+    def bytes_used(self):
+        return int(load().nsli_pool_bytes_used(self._h))
+
+    def launch_count(self):
+        return int(load().nsli_pool_launch_count(self._h))
+
+    def sync(self):
+        self._check(load().nsli_pool_sync(self._h), "nsli_pool_sync")

@@ -1,0 +1,114 @@
+"""Serving loop with continuous batching over an nsli pool.
+
+Requests (feasibility problems of mixed sizes) are queued on arrival and
+admitted in arrival order as soon as they fit the pool's memory; every
+admitted problem stays on the device (A, x, b) and advances with all other
+live problems, one grouped launch per round; finished problems are retired
+(x and the binary64 check read back, memory released), which makes room for
+queued ones.  With `tick_s` set, the right-hand side of each problem moves
+with wall-clock time: tick k = floor((now - arrival) / tick_s).
+
+The scheduling is host logic; every arithmetic step runs in libnsli.so.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import nsli
+
+
+@dataclass
+class Request:
+    rid: int
+    A: object
+    b0: object
+    x0: object
+    Av: object = None
+    params: dict = field(default_factory=dict)
+    arrival: float = 0.0
+    admitted: float | None = None
+    finished: float | None = None
+    status: int | None = None
+    iters: int = 0
+    x: np.ndarray | None = None
+    max_viol: float | None = None
+    slot: int | None = None
+
+    @property
+    def latency(self):
+        return None if self.finished is None else self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, storage="bf16", max_bytes=0, tick_s=None, rounds_per_poll=4, stream=None,
+                 clock=time.perf_counter):
+        self.pool = nsli.Pool(storage=storage, max_bytes=max_bytes, stream=stream)
+        self.tick_s = tick_s
+        self.rounds = rounds_per_poll
+        self.clock = clock
+        self.queue: list[Request] = []
+        self.live: dict[int, Request] = {}
+        self.done: list[Request] = []
+        self.rounds_run = 0
+        self.problem_iterations = 0
+
+    def submit(self, req: Request):
+        if req.arrival == 0.0:
+            req.arrival = self.clock()
+        self.queue.append(req)
+        return req
+
+    def _admit(self):
+        while self.queue:
+            r = self.queue[0]
+            slot = self.pool.add(r.A, r.b0, r.x0, Av=r.Av, **r.params)
+            if slot is None:        # does not fit now: wait for memory to free up
+                break
+            self.queue.pop(0)
+            r.slot = slot
+            r.admitted = self.clock()
+            self.live[slot] = r
+
+    def _ticks(self):
+        if self.tick_s is None or not self.live:
+            return
+        now = self.clock()
+        slots = list(self.live.keys())
+        ticks = [int((now - self.live[s].arrival) / self.tick_s) for s in slots]
+        self.pool.set_ticks(slots, ticks)
+
+    def pump(self):
+        """Admit what fits, run a few rounds, retire what finished."""
+        self._admit()
+        if not self.live:
+            return 0
+        self._ticks()
+        nlive = len(self.live)
+        self.pool.step(self.rounds)
+        self.rounds_run += self.rounds
+        finished = self.pool.poll()
+        now = self.clock()
+        for slot, status, iters in finished:
+            r = self.live.pop(slot)
+            r.status, r.iters = status, iters
+            r.x = self.pool.get_x(slot, int(r.x0.shape[0]))
+            r.max_viol = self.pool.residual_max(slot)[0]
+            r.finished = now
+            self.pool.remove(slot)
+            self.done.append(r)
+        self.problem_iterations += nlive * self.rounds  # upper bound: finished problems skip rounds
+        return len(finished)
+
+    def drain(self, timeout_s=None):
+        t0 = self.clock()
+        while self.queue or self.live:
+            self.pump()
+            if timeout_s is not None and self.clock() - t0 > timeout_s:
+                break
+        return self.done
+
+    def close(self):
+        self.pool.close()
