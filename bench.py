@@ -65,6 +65,9 @@ def parse_args():
                     help="batched tensor-core workload measured in the same run ('' for none)")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the batched workload (profiling entry)")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of the serving stream measured in the same run (0: none)")
+    ap.add_argument("--serving-only", action="store_true", help="time only the serving stream")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -186,6 +189,32 @@ def cpu_baseline(p, m_full, seconds, rho):
                                                                       rows, m_full)}
 
 
+def time_model_system(nsli, seeds=30):
+    """The model system (n = 256, m = 513, binary64 storage, lambda = 1,
+    ||dx|| < 1e-8): solve time per seed through nsli_solve (graph blocks,
+    state polls and the binary64 confirmation included)."""
+    from paper_2003_09956_gb300 import workloads
+
+    times, iters, viol = [], [], []
+    for sd in range(seeds):
+        p = workloads.model_system(256, seed=sd)
+        with nsli.Solver(p["A"], p["b0"], p["x0"], storage="f64") as s:
+            if sd == 0:
+                s.solve(stop="step", eps=1e-8, max_iter=100000, block_iters=64)   # warm-up (graph capture)
+                s.set_x(p["x0"])
+            t0 = time.perf_counter()
+            r = s.solve(stop="step", eps=1e-8, max_iter=100000, block_iters=64)
+            times.append(time.perf_counter() - t0)
+            iters.append(r["iters"])
+            viol.append(r["max_viol"] / np.abs(p["b0"]).max())
+    t = np.array(times) * 1e3
+    return {"workload": "model system n=256 m=513 f64, STEP 1e-8", "seeds": seeds,
+            "p50_solve_ms": float(np.percentile(t, 50)), "p99_solve_ms": float(np.percentile(t, 99)),
+            "median_iterations": float(np.median(iters)),
+            "us_per_iteration": float(np.median(t * 1e3 / np.array(iters))),
+            "max_rel_violation_f64": float(np.max(viol))}
+
+
 def time_batched(nsli, torch, name, steps, warmup):
     """Batch iterations of P problems sharing one bf16 A on the tensor cores."""
     from paper_2003_09956_gb300 import workloads
@@ -218,6 +247,79 @@ def time_batched(nsli, torch, name, steps, warmup):
             "ms_per_batch_iteration": ms, "A_stream_gbs": abytes / (ms / 1e3) / 1e9,
             "tensor_tflops": flops / (ms / 1e3) / 1e12, "gpu_launches": launches,
             "max_viol_f64_first_problems": [float(v) for v in mv[:4]]}
+
+
+SERVE = {"rate": 200.0, "tick_s": 0.010, "rho": 1e-4, "eps": 1e-6, "max_iter": 300, "seed": 2010,
+         "classes": [int(round(512 * 2 ** (k / 2))) for k in range(11)], "c": [2, 4, 8]}
+
+
+def time_serving(nsli, torch, seconds):
+    """Poisson stream of dense random systems of mixed sizes (n log-uniform in
+    [512, 16384] over 11 log-spaced classes, m = c n with c in {2, 4, 8}, bf16)
+    served with continuous batching; each request gets its own x0 and an
+    iteration budget; b moves with 10 ms wall-clock ticks."""
+    from paper_2003_09956_gb300 import serve, workloads
+
+    cfg = SERVE
+    rng = np.random.default_rng(cfg["seed"])
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / cfg["rate"])
+        if t > seconds:
+            break
+        arrivals.append((t, int(rng.integers(0, len(cfg["classes"]))), int(rng.integers(0, 3)),
+                         int(rng.integers(1 << 30))))
+    # one template system per (size class, c) drawn, resident on the device
+    t_gen = time.perf_counter()
+    templates = {}
+    for _, k, ci, _ in arrivals:
+        if (k, ci) in templates:
+            continue
+        n = cfg["classes"][k]
+        m = cfg["c"][ci] * n
+        p = workloads.dense_system(m, n, seed=cfg["seed"] + 100 * k + ci)
+        templates[(k, ci)] = (torch.from_numpy(p["A"]).cuda(), p["b0"], p["Av"], n)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    params = dict(stop="maxviol_rel", eps=cfg["eps"], max_iter=cfg["max_iter"], rho=cfg["rho"])
+    srv = serve.Server(storage="bf16", tick_s=cfg["tick_s"], rounds_per_poll=2)
+    clock = time.perf_counter
+    t0 = clock()
+    i = 0
+    grace = seconds
+    while True:
+        now = clock() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            ta, k, ci, sx = arrivals[i]
+            A, b0, Av, n = templates[(k, ci)]
+            x0 = np.random.default_rng(sx).normal(0.0, 5.0, n).astype(np.float32).astype(np.float64)
+            srv.submit(serve.Request(i, A, b0, x0, Av=Av, params=params, arrival=t0 + ta))
+            i += 1
+        if srv.queue or srv.live:
+            srv.pump()
+        elif i < len(arrivals):
+            time.sleep(max(0.0, min(0.001, arrivals[i][0] - now)))
+        if (i >= len(arrivals) and not srv.queue and not srv.live) or now > seconds + grace:
+            break
+    elapsed = clock() - t0
+    done = srv.done
+    lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
+    feas = [r for r in done if r.status == nsli.OK]
+    iters = srv.problem_iterations
+    out = {"requests": len(arrivals), "arrival_rate_per_s": cfg["rate"], "stream_s": seconds,
+           "completed": len(done), "feasible": len(feas), "not_converged_within_budget": len(done) - len(feas),
+           "left_queued": len(srv.queue), "left_running": len(srv.live),
+           "iteration_budget": cfg["max_iter"], "elapsed_s": elapsed,
+           "solves_per_s": len(done) / elapsed, "problem_iterations_per_s": iters / elapsed,
+           "p50_time_to_result_ms": float(np.percentile(lat, 50) * 1e3),
+           "p99_time_to_result_ms": float(np.percentile(lat, 99) * 1e3),
+           "p50_time_to_feasible_ms": float(np.percentile([r.latency for r in feas], 50) * 1e3) if feas else None,
+           "p99_time_to_feasible_ms": float(np.percentile([r.latency for r in feas], 99) * 1e3) if feas else None,
+           "grouped_round_gbs": srv.bytes_streamed / max(srv.busy_s, 1e-9) / 1e9,
+           "gpu_launches": srv.pool.launch_count(), "template_setup_s": t_gen,
+           "ticks": "%g s wall clock" % cfg["tick_s"]}
+    srv.close()
+    return out
 
 
 def dist_setup():
@@ -312,6 +414,12 @@ def main():
     from paper_2003_09956_gb300 import nsli, workloads
 
     nsli.load()
+    if args.serving_only:
+        r = time_serving(nsli, torch, args.serve_seconds)
+        if rank == 0:
+            print(json.dumps({"metric": "serving solves/sec", "value": r["solves_per_s"], "unit": "solves/s",
+                              "config": {"workload": "poisson-200/s mixed-size bf16 stream"}, **r}), flush=True)
+        return 0
     if args.batched_only:
         r = time_batched(nsli, torch, args.batched, args.steps, max(3, args.warmup))
         if rank == 0:
@@ -377,8 +485,11 @@ def main():
                         "map_frac_of_measured_hbm": vb / (r["map_ms_avg"] / 1000.0) / 1e9 / peak,
                         "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
 
+    variants["model_system_f64"] = time_model_system(nsli)
     if args.batched:
         variants["batched_bf16"] = time_batched(nsli, torch, args.batched, min(K, 100), W)
+    if args.serve_seconds > 0 and world == 1:
+        variants["serving_bf16"] = time_serving(nsli, torch, args.serve_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -36,6 +36,11 @@ class Request:
     x: np.ndarray | None = None
     max_viol: float | None = None
     slot: int | None = None
+    stored_bytes: int = 0
+
+    def __post_init__(self):
+        m, n = int(self.A.shape[0]), int(self.A.shape[1])
+        self.stored_bytes = m * n * 2   # bf16 rows streamed per iteration
 
     @property
     def latency(self):
@@ -53,7 +58,9 @@ class Server:
         self.live: dict[int, Request] = {}
         self.done: list[Request] = []
         self.rounds_run = 0
-        self.problem_iterations = 0
+        self.problem_iterations = 0   # iterations of every problem, running or finished
+        self.bytes_streamed = 0       # bytes of A read by the grouped Map launches
+        self.busy_s = 0.0             # wall time inside rounds + polls
 
     def submit(self, req: Request):
         if req.arrival == 0.0:
@@ -86,11 +93,22 @@ class Server:
         if not self.live:
             return 0
         self._ticks()
-        nlive = len(self.live)
+        t0 = self.clock()
+        running = [r for r in self.live.values() if r.status is None]
         self.pool.step(self.rounds)
         self.rounds_run += self.rounds
         finished = self.pool.poll()
         now = self.clock()
+        self.busy_s += now - t0
+        fin_slots = {f[0]: f[2] for f in finished}
+        for r in running:
+            # a running problem advances one iteration per round until it stops
+            done_iters = fin_slots.get(r.slot)
+            step = self.rounds if done_iters is None else max(0, done_iters - r.iters)
+            self.problem_iterations += step
+            self.bytes_streamed += step * r.stored_bytes
+            if done_iters is None:
+                r.iters += self.rounds
         for slot, status, iters in finished:
             r = self.live.pop(slot)
             r.status, r.iters = status, iters
@@ -99,7 +117,6 @@ class Server:
             r.finished = now
             self.pool.remove(slot)
             self.done.append(r)
-        self.problem_iterations += nlive * self.rounds  # upper bound: finished problems skip rounds
         return len(finished)
 
     def drain(self, timeout_s=None):
