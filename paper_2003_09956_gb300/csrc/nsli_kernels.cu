@@ -257,8 +257,10 @@ template <int RG, typename T> __device__ __forceinline__ T warp_fold_rows(const 
 // the CTA-level sum of the positive slices goes to part_row (ld elements of
 // the accumulation type), the CTA's counters to *stat_out.  Threads
 // t < nt own vectors t + v * nt (v < vpt_used <= VPT); the others only take
-// part in the barriers and reductions (with zero partial sums).
-template <int S, int VPT, bool GUARD>
+// part in the barriers and reductions (with zero partial sums).  PARTIAL is
+// false when every thread of the block owns VPT vectors (nt == blockDim.x,
+// vpt_used == VPT), which keeps the guard-free instances free of tests.
+template <int S, int VPT, bool GUARD, bool PARTIAL>
 __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_begin, const long long row_end,
                                          void *part_row, PartStat *stat_out, const int nt, const int vpt_used)
 {
@@ -323,7 +325,7 @@ __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_b
     for (int v = 0; v < VPT; ++v) {
         const int j = tid + v * nt;
         voff[v] = j * 16;
-        vok[v] = v < vpt_used && tid < nt && (!GUARD || j < p.nv);
+        vok[v] = (!PARTIAL || (v < vpt_used && tid < nt)) && (!GUARD || j < p.nv);
     }
 
     Acc xr[VPT][EPV];
@@ -507,8 +509,8 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_kernel(const MapArgs 
     const long long b = blockIdx.x;
     const long long row_begin = b * p.rows_base + (b < p.rows_rem ? b : (long long)p.rows_rem);
     const long long row_end = row_begin + p.rows_base + (b < p.rows_rem ? 1 : 0);
-    map_body<S, VPT, GUARD>(p, row_begin, row_end, static_cast<Acc *>(p.part_y) + b * p.ld, p.part_stat + b,
-                            (int)blockDim.x, VPT);
+    map_body<S, VPT, GUARD, false>(p, row_begin, row_end, static_cast<Acc *>(p.part_y) + b * p.ld,
+                                   p.part_stat + b, (int)blockDim.x, VPT);
 }
 
 // Many problems in one launch: CTA b maps work item b (a block of rows of
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_group_kernel(const Gr
     const GroupProblem &gp = probs[it.prob];
     if (*(volatile int *)&gp.map.st->done)
         return;
-    map_body<S, VPT, true>(gp.map, it.row_begin, it.row_end,
+    map_body<S, VPT, true, true>(gp.map, it.row_begin, it.row_end,
                            static_cast<Acc *>(gp.map.part_y) + (long long)it.part * gp.map.ld,
                            gp.map.part_stat + it.part, gp.nt, gp.vpt);
 }
