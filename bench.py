@@ -323,10 +323,9 @@ def time_serving(nsli, torch, seconds):
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2003_09956_gb300 import replicas
+
+    return replicas.rank_info()
 
 
 def run_reference(args):
@@ -361,6 +360,8 @@ def run_reference(args):
 
 
 def time_storage(nsli, torch, p, storage, w, steps, warmup, dist, world):
+    from paper_2003_09956_gb300 import replicas
+
     """Create the solver for one storage type, warm up, time `steps`
     iterations (graph replays), then one kernel-by-kernel pass."""
     stream = torch.cuda.Stream()
@@ -370,8 +371,7 @@ def time_storage(nsli, torch, p, storage, w, steps, warmup, dist, world):
     s.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     l0 = s.launch_count()
     with torch.cuda.stream(stream):
@@ -381,13 +381,8 @@ def time_storage(nsli, torch, p, storage, w, steps, warmup, dist, world):
     e1.synchronize()
     torch.cuda.synchronize()
     launches = s.launch_count() - l0
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    replicas.barrier(dist)
+    ms = replicas.max_over_ranks(dist, e0.elapsed_time(e1), device="cuda")
     kpass = min(steps, 100)
     map_ms, red_ms = s.iterate_timed(kpass, rho=w["rho"])
     mv, mn = s.residual_max()
@@ -411,7 +406,7 @@ def main():
         dist = tdist
     else:
         torch.cuda.set_device(0)
-    from paper_2003_09956_gb300 import nsli, workloads
+    from paper_2003_09956_gb300 import nsli, replicas, workloads
 
     nsli.load()
     if args.serving_only:
@@ -453,22 +448,17 @@ def main():
         b_pin[k] = snaps[k]
     x_pin = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
     s.sync()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     t0 = time.perf_counter()
     for k in range(Ke):
         s.update_b(b_pin[k], tick=0)
         s.iterate(1, rho=0.0)
         s.get_x(out=x_pin)
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
     s.close()
 
     peak, peak_kind = measured_peak()
-    value = world * K / (main_run["ms"] / 1000.0)
+    value = replicas.aggregate_rate(world, K, main_run["ms"] / 1000.0)
     mb = map_bytes(m, n, args.storage)
     achieved = mb / (main_run["map_ms_avg"] / 1000.0) / 1e9
     traffic = profiled_traffic(args.workload, args.storage)
@@ -513,7 +503,7 @@ def main():
                      "map_ms_avg": main_run["map_ms_avg"], "reduce_ms_avg": main_run["reduce_ms_avg"],
                      "kernel_pass_ms_per_step": main_run["kernel_pass_ms_per_step"],
                      "step_gbs": step_bytes(m, n, args.storage) * value / world / 1e9},
-        "e2e": {"value": world * Ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": m * 8,
+        "e2e": {"value": replicas.aggregate_rate(world, Ke, t_e2e), "unit": UNIT, "h2d_bytes_per_step": m * 8,
                 "d2h_bytes_per_step": n * 8},
         "gpu_launches": main_run["launches"],
         "clocks": clk,

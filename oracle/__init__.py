@@ -23,6 +23,7 @@ forms, brute force on small systems, invariants and library routines.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -36,6 +37,20 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libnsli_oracle.so")
 _lock = threading.Lock()
 _lib = None
+_override = None
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Test support: run the oracle's functions on another build of
+    nsli_oracle.c (used to check that the pins catch planted mistakes)."""
+    global _lib, _override
+    old_lib, old_override = _lib, _override
+    _lib, _override = None, path
+    try:
+        yield
+    finally:
+        _lib, _override = old_lib, old_override
 
 RULE_RELAXED = 0
 RULE_MODAP = 1
@@ -50,6 +65,14 @@ OK = 0
 NOT_CONVERGED = 1
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file into a shared library (same flags)."""
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build`` (idempotent)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
@@ -57,9 +80,7 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_source(_SRC, tmp)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -69,7 +90,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(_override if _override else build())
         i64, dbl, ip = ctypes.c_int64, ctypes.c_double, ctypes.c_int
         P = ctypes.c_void_p
         lib.oracle_norms2.argtypes = [i64, i64, P, P]

@@ -380,3 +380,29 @@ def test_binary32_entry_points_match_double_entry_points():
     np.testing.assert_array_equal(m1["y"], m2["y"])
     np.testing.assert_array_equal(m1["r"], m2["r"])
     assert m1["h"] == m2["h"]
+
+
+def test_maxviol_rel_threshold_is_relative_to_max_b():
+    """The relative rule stops when max_i r_i <= eps * max_i |b_i|: with
+    max|b| = 1000 and eps = 1e-6 the threshold is 1e-3, so a point violating
+    one row by 5e-4 is accepted at once and one violating it by 2e-3 is not."""
+    A = np.array([[1.0, 0.0], [0.0, 1.0]])
+    b = np.array([1000.0, 1.0])
+    res = oracle.solve(A, b, np.array([1000.0 + 5e-4, 0.0]), stop=oracle.STOP_MAXVIOL_REL,
+                       eps=1e-6, max_iter=0)
+    assert res["status"] == oracle.OK and res["iters"] == 0
+    res = oracle.solve(A, b, np.array([1000.0 + 2e-3, 0.0]), stop=oracle.STOP_MAXVIOL_REL,
+                       eps=1e-6, max_iter=0)
+    assert res["status"] == oracle.NOT_CONVERGED
+
+
+def test_only_strictly_violated_rows_count():
+    """Eq. 7 / Eq. 8: a row contributes iff r_i > 0.  Rows with r_i = 0
+    exactly or slightly negative add nothing to y and are not counted in h."""
+    A = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 1.0]])
+    b = np.array([1.0, 1.0, 1.0 + 5e-4])
+    n2, _ = oracle.norms2(A)
+    mr = oracle.map_reduce(A, b, n2, np.array([3.0, 1.0]))   # r = (2, 0, -5e-4)
+    assert mr["h"] == 1
+    np.testing.assert_array_equal(mr["y"], [2.0, 0.0])
+    assert mr["maxviol"] == 2.0
