@@ -551,6 +551,7 @@ __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceSh
     if (threadIdx.x < 32) {
         long long h = 0;
         double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+#pragma unroll 4
         for (int g = lane; g < G; g += 32) {
             const PartStat q = ps[g];
             h += q.h;
@@ -602,8 +603,14 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
         double yj = 0.0;
         if (j < p.ld) {
             const Acc *py = static_cast<const Acc *>(p.part_y);
+            // the partial rows g = grp, grp + 8, ... added in that order in
+            // the accumulation type (binary64 is slow on this part), the
+            // eight group sums then in binary64
+            Acc t = Acc(0);
+#pragma unroll 8
             for (int g = grp; g < p.G; g += 8)
-                yj += (double)py[(long long)g * p.ld + j];
+                t += py[(long long)g * p.ld + j];
+            yj = (double)t;
         }
         sh.part[grp][lane] = yj;
     }
@@ -647,6 +654,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
     if (step) {
         if (grp == 0) {
             double v = 0.0;
+#pragma unroll 4
             for (int q = lane; q < nblk; q += 32)
                 v += __ldcg(p.part_dx + q);
             v = warp_sum(v);
@@ -733,8 +741,11 @@ __global__ void __launch_bounds__(256) reduce_only_kernel(const ReduceArgs p, do
     double yj = 0.0;
     if (j < p.ld) {
         const Acc *py = static_cast<const Acc *>(p.part_y);
+        Acc t = Acc(0);
+#pragma unroll 8
         for (int g = grp; g < p.G; g += 8)
-            yj += (double)py[(long long)g * p.ld + j];
+            t += py[(long long)g * p.ld + j];
+        yj = (double)t;
     }
     sh.part[grp][lane] = yj;
     __syncthreads();
