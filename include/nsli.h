@@ -178,6 +178,14 @@ int nsli_set_x(nsli_handle h, const double *x);
 int nsli_get_stored_rows(nsli_handle h, int64_t row0, int64_t rows, double *out);
 int nsli_get_norms2(nsli_handle h, double *out);
 
+/* Failure-detection test (no GPU fault): one Map launch in which CTA 0 never
+ * issues the bulk copy of its row slot `slot`, so its threads wait on a
+ * barrier that nothing completes.  The bounded waits (about two seconds)
+ * expire, the CTA records the timeout, waits (bounded) for its other copies
+ * and returns.  Returns NSLI_ERR_TIMEOUT when detection works (NSLI_OK if
+ * slot is beyond CTA 0's rows); the handle stays usable.  Synchronises. */
+int nsli_test_inject_timeout(nsli_handle h, int32_t slot);
+
 /* Progress of the last nsli_iterate / nsli_solve (device state).  The
  * binary64 fields of out are those of the last check made, or 0.  Synchronises. */
 int nsli_get_result(nsli_handle h, nsli_result *out);

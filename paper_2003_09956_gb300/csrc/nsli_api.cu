@@ -178,6 +178,7 @@ MapArgs map_args(nsli_solver *h)
     a.nstage = h->nstage;
     a.stage_stride = h->stage_stride;
     a.ignore_done = 0;
+    a.skip_slot = -1;
     return a;
 }
 
@@ -764,6 +765,22 @@ int nsli_set_x(nsli_handle h, const double *x)
        "convert x");
     h->launches += 1;
     return read_flags(h);
+}
+
+int nsli_test_inject_timeout(nsli_handle h, int32_t slot)
+{
+    if (!h || slot < 0)
+        return NSLI_ERR_ARG;
+    MapArgs ma = map_args(h);
+    ma.ignore_done = 1;
+    ma.skip_slot = slot;
+    CK(cudaMemsetAsync(&h->st->error, 0, sizeof(int), h->stream), "clear error");
+    CK(map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
+    h->launches += 1;
+    int rc = read_state(h);
+    CK(cudaMemsetAsync(&h->st->error, 0, sizeof(int), h->stream), "clear error");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return rc;
 }
 
 int nsli_get_stored_rows(nsli_handle h, int64_t row0, int64_t rows, double *out)

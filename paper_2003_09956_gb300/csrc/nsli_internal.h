@@ -80,6 +80,7 @@ struct MapArgs {
     int nstage;
     int stage_stride;      // bytes per stage in shared memory
     int ignore_done;       // run even when the done flag is set
+    int skip_slot;         // failure injection: CTA 0 never issues this slot (-1: none)
 };
 
 struct ReduceArgs {

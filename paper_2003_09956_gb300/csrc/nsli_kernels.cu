@@ -289,7 +289,10 @@ __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_b
     const unsigned char *Mb = static_cast<const unsigned char *>(p.meta);
 
     // issue the copies of slot s into its stage (thread 0 only)
+    const int skip = (blockIdx.x == 0) ? p.skip_slot : -1;
     auto issue = [&](int s) {
+        if (s == skip)
+            return;  // failure injection: a wait that nothing will complete
         const int stage = s % p.nstage;
         const long long r0 = row_begin + (long long)s * R;
         const long long left = row_end - r0;

@@ -63,7 +63,7 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
            "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
-           "nsli_get_stored_rows", "nsli_get_norms2",
+           "nsli_get_stored_rows", "nsli_get_norms2", "nsli_test_inject_timeout",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
            "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc",
            "nsli_batch_create", "nsli_batch_iterate", "nsli_batch_map_reduce", "nsli_batch_get_x",
@@ -113,6 +113,8 @@ def load(path: str | None = None):
         lib.nsli_set_x.restype = ctypes.c_int
         lib.nsli_get_stored_rows.argtypes = [H, i64, i64, P]
         lib.nsli_get_stored_rows.restype = ctypes.c_int
+        lib.nsli_test_inject_timeout.argtypes = [H, i32]
+        lib.nsli_test_inject_timeout.restype = ctypes.c_int
         lib.nsli_get_norms2.argtypes = [H, P]
         lib.nsli_get_norms2.restype = ctypes.c_int
         lib.nsli_get_result.argtypes = [H, ctypes.POINTER(nsli_result)]
@@ -367,6 +369,11 @@ class Solver:
         _check(load().nsli_get_stored_rows(self._h, int(row0), int(rows), _ptr(out)),
                "nsli_get_stored_rows", self._h)
         return out
+
+    def inject_timeout(self, slot=1):
+        """Failure-detection test: returns the status of a Map launch whose
+        first CTA waits on a bulk copy that is never issued."""
+        return int(load().nsli_test_inject_timeout(self._h, int(slot)))
 
     def norms2(self):
         out = np.empty(self.m, np.float64)

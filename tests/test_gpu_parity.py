@@ -346,11 +346,16 @@ def test_full_size_32768x8192_one_step(cfg2_system, storage):
         check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
 
 
-def test_full_size_131072x16384_f32_one_step_and_fejer():
+@pytest.fixture(scope="module")
+def cfg3_system():
+    return workloads.dense_system(131072, 16384, seed=2005)
+
+
+def test_full_size_131072x16384_f32_one_step_and_fejer(cfg3_system):
     """The benchmark's workload and launch shape: one Map/Reduce against the
     oracle, then 6 stationary iterations whose distance to the interior point
     z must not grow (Fejer property, any size)."""
-    p = workloads.dense_system(131072, 16384, seed=2005)
+    p = cfg3_system
     with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage="f32") as s:
         check_map_reduce(s, p["A"], p["b0"], p["x0"], "f32")
         d_prev = np.linalg.norm(s.get_x() - p["z"])
@@ -359,3 +364,17 @@ def test_full_size_131072x16384_f32_one_step_and_fejer():
             d = np.linalg.norm(s.get_x() - p["z"])
             assert d <= d_prev * (1 + 1e-6)
             d_prev = d
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_full_size_131072x16384_quantized_one_step(cfg3_system, storage):
+    """The bf16 and fp8 storage of the benchmark system: stored values and
+    one Map/Reduce against the oracle on the oracle's own quantization."""
+    p = cfg3_system
+    A_eff = stored_values(p["A"], storage)
+    with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        rows = np.random.default_rng(5).integers(0, 131072, 64)
+        for r in rows:
+            np.testing.assert_array_equal(s.stored_rows(int(r), 1)[0], A_eff[r].astype(np.float64))
+        s.iterate(0, rho=1e-4)
+        check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
