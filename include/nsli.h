@@ -121,9 +121,10 @@ typedef struct {
  *             stream: iteration blocks are captured into CUDA graphs), or
  *             NULL to let the handle create and own a non-blocking stream.
  * Errors: NSLI_ERR_ARG (m, n < 1, lda < n, bad enum, NULL required pointer),
- * NSLI_ERR_ZERO_ROW, NSLI_ERR_NONFINITE, NSLI_ERR_OOM, NSLI_ERR_CUDA,
- * NSLI_ERR_UNSUPPORTED (n beyond the register-resident row limit: 16384 for
- * binary32 / bf16 / fp8 storage, 8192 for binary64).  On error *out is NULL
+ * NSLI_ERR_ZERO_ROW, NSLI_ERR_NONFINITE, NSLI_ERR_OOM, NSLI_ERR_CUDA.  Rows
+ * up to 16384 entries (binary32 / bf16 / fp8; 8192 for binary64) are held
+ * in registers while streamed through shared memory; longer rows use a
+ * chunked two-pass Map that re-reads violated rows from L2.  On error *out is NULL
  * and nothing is leaked.  The handle owns all its device memory until
  * nsli_destroy. */
 int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage,

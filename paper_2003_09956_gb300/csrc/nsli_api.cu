@@ -132,9 +132,20 @@ int choose_config(nsli_solver *h)
             break;
         }
     }
-    if (h->vpt == 0)
-        return set_err(h, NSLI_ERR_UNSUPPORTED,
-                       "n too large for the register-resident row kernel of this build");
+    if (h->vpt == 0) {
+        // long rows: the chunked two-pass kernel (no shared-memory ring)
+        h->consumers = 512;
+        h->guard = true;
+        h->R = 1;
+        h->nstage = 0;
+        h->stage_stride = 0;
+        h->smem = 0;
+        h->G = (int)std::min<long long>(h->num_sms, h->m);
+        h->rows_base = h->m / h->G;
+        h->rows_rem = (int)(h->m % h->G);
+        h->red_grid = (int)((h->ld + kReduceCols - 1) / kReduceCols);
+        return NSLI_OK;
+    }
     h->consumers = (int)round_up((h->nv + h->vpt - 1) / h->vpt, 32);
     // bytes of A per ring slot: 64 KiB unless NSLI_MAP_SLOT_KB (4..96) overrides it
     int slot_target = 65536;
@@ -771,6 +782,8 @@ int nsli_test_inject_timeout(nsli_handle h, int32_t slot)
 {
     if (!h || slot < 0)
         return NSLI_ERR_ARG;
+    if (h->vpt == 0)
+        return set_err(h, NSLI_ERR_UNSUPPORTED, "long rows are not streamed through bulk copies");
     MapArgs ma = map_args(h);
     ma.ignore_done = 1;
     ma.skip_slot = slot;
@@ -1046,6 +1059,12 @@ int nsli_pool_add(nsli_pool p, int64_t m, int64_t n, const float *A, int64_t lda
     int rc = nsli_create(&h, m, n, p->storage, NSLI_F32, A, lda, b0, nullptr, Av, x0, p->stream);
     if (rc != NSLI_OK)
         return perr(p, rc, "create problem");
+    if (h->vpt == 0) {
+        h->stream = nullptr;
+        free_all(h);
+        delete h;
+        return perr(p, NSLI_ERR_UNSUPPORTED, "the pool serves rows up to the register-resident limit");
+    }
     // control state of the problem's run
     if ((rc = validate_params(h, prm)) != NSLI_OK || (rc = begin_run(h, prm, prm->stop, prm->max_iter)) != NSLI_OK) {
         h->stream = nullptr;

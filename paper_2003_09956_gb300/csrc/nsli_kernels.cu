@@ -533,6 +533,174 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_group_kernel(const Gr
                            gp.map.part_stat + it.part, gp.nt, gp.vpt);
 }
 
+// --------------------------------------------------- Map, long rows --------
+//
+// Rows longer than the register-resident limit (n > 16384 for 4-, 2- and
+// 1-byte storage, n > 8192 for binary64).  The CTA takes its rows four at a
+// time and walks them in column chunks of 1024 16-byte vectors: thread t
+// owns vectors t and t + 512 of every chunk.  Pass 1 streams the chunk of
+// the four rows from HBM with 16-byte loads and accumulates the dots against
+// the chunk of x (loaded once per four rows); one block reduction gives the
+// four residuals.  Pass 2 re-reads the chunks of the violated rows (now in
+// L2) and adds r_i / ||a_i||^2 * a_i into the CTA's row of partial sums in
+// global memory, each thread its own columns (no atomics, a fixed order).
+constexpr int kLongThreads = 512;
+constexpr int kLongVPT = 2;
+constexpr int kLongRows = 4;
+
+template <int S>
+__global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs p)
+{
+    using Tr = Traits<S>;
+    using Acc = typename Tr::acc;
+    using Meta = typename Tr::meta;
+    constexpr int EPV = Tr::EPV;
+    constexpr int RG = kLongRows;
+    constexpr int W = 32 / RG;
+
+    DevState *st = p.st;
+    if (!p.ignore_done && *(volatile int *)&st->done)
+        return;
+    __shared__ Acc red[2][RG][32];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwarps = kLongThreads / 32;
+    const long long b = blockIdx.x;
+    const long long row_begin = b * p.rows_base + (b < p.rows_rem ? b : (long long)p.rows_rem);
+    const long long row_end = row_begin + p.rows_base + (b < p.rows_rem ? 1 : 0);
+    const long long nv = p.nv;
+    const long long chunk = (long long)kLongThreads * kLongVPT;
+    const int nchunks = (int)((nv + chunk - 1) / chunk);
+    const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
+    const Meta *meta = static_cast<const Meta *>(p.meta);
+    const Acc *xg = static_cast<const Acc *>(p.x);
+    Acc *py = static_cast<Acc *>(p.part_y) + b * p.ld;
+    for (long long e = tid; e < p.ld; e += kLongThreads)
+        py[e] = Acc(0);
+    const Acc tk = (Acc)((double)st->tick * st->rho);
+
+    long long h_loc = 0;
+    Acc mv = neg_inf<Acc>(), mn = neg_inf<Acc>(), mb = Acc(0);
+    int grp_counter = 0;
+    for (long long r0 = row_begin; r0 < row_end; r0 += RG) {
+        const int gr = (int)((row_end - r0) < RG ? (row_end - r0) : RG);
+        Acc pe[RG], po[RG];
+#pragma unroll
+        for (int rr = 0; rr < RG; ++rr) {
+            pe[rr] = Acc(0);
+            po[rr] = Acc(0);
+        }
+        // ---- pass 1: dots of the group's rows, chunk by chunk
+        for (int c = 0; c < nchunks; ++c) {
+            long long j[kLongVPT];
+            bool ok[kLongVPT];
+            Acc xv[kLongVPT][EPV];
+            uint4 q[RG][kLongVPT];
+#pragma unroll
+            for (int v = 0; v < kLongVPT; ++v) {
+                j[v] = (long long)c * chunk + tid + v * kLongThreads;
+                ok[v] = j[v] < nv;
+#pragma unroll
+                for (int rr = 0; rr < RG; ++rr)
+                    q[rr][v] = (ok[v] && rr < gr)
+                                   ? __ldg(reinterpret_cast<const uint4 *>(Ab + (r0 + rr) * (long long)p.row_bytes) + j[v])
+                                   : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e)
+                    xv[v][e] = ok[v] ? __ldg(xg + j[v] * EPV + e) : Acc(0);
+            }
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+#pragma unroll
+                for (int v = 0; v < kLongVPT; ++v) {
+                    Acc a[EPV];
+                    decode<S>(q[rr][v], a);
+#pragma unroll
+                    for (int e = 0; e < EPV; e += 2)
+                        fma2(pe[rr], po[rr], a[e], a[e + 1], xv[v][e], xv[v][e + 1]);
+                }
+            }
+        }
+        Acc acc[RG];
+#pragma unroll
+        for (int rr = 0; rr < RG; ++rr)
+            acc[rr] = pe[rr] + po[rr];
+        Acc *rb = &red[grp_counter & 1][0][0];
+        const Acc wsum = warp_fold_rows<RG>(acc, lane);
+        if ((lane & (W - 1)) == 0)
+            rb[(lane / W) * 32 + warp] = wsum;
+        __syncthreads();
+        Acc tsum = Acc(0);
+        {
+            const int qq = lane / W, i = lane % W;
+            for (int w = i; w < nwarps; w += W)
+                tsum += rb[qq * 32 + w];
+#pragma unroll
+            for (int off = W / 2; off > 0; off >>= 1)
+                tsum += __shfl_xor_sync(0xffffffffu, tsum, off);
+        }
+        Acc cr[RG];
+        bool any = false;
+#pragma unroll
+        for (int rr = 0; rr < RG; ++rr) {
+            const Acc dot = __shfl_sync(0xffffffffu, tsum, rr * W);
+            const bool valid = rr < gr;
+            const Meta md = meta[r0 + (valid ? rr : 0)];
+            const Acc sc = (Acc)meta_scale(md);
+            const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
+            const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
+            const bool viol = valid && ri > Acc(0);
+            cr[rr] = viol ? ((S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2) : Acc(0);
+            any = any || viol;
+            if (warp == 0 && valid) {
+                h_loc += viol ? 1 : 0;
+                mv = ri > mv ? ri : mv;
+                const Acc rn = ri * (Acc)md.inv_n;
+                mn = rn > mn ? rn : mn;
+                const Acc ab = bi < Acc(0) ? -bi : bi;
+                mb = ab > mb ? ab : mb;
+            }
+        }
+        // ---- pass 2: add the violated rows' slices (rows re-read from L2)
+        if (any) {
+            for (int c = 0; c < nchunks; ++c) {
+#pragma unroll
+                for (int v = 0; v < kLongVPT; ++v) {
+                    const long long jj = (long long)c * chunk + tid + v * kLongThreads;
+                    if (jj >= nv)
+                        continue;
+                    Acc y[EPV];
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e)
+                        y[e] = py[jj * EPV + e];
+#pragma unroll
+                    for (int rr = 0; rr < RG; ++rr) {
+                        if (cr[rr] != Acc(0)) {
+                            Acc a[EPV];
+                            decode<S>(__ldg(reinterpret_cast<const uint4 *>(Ab + (r0 + rr) * (long long)p.row_bytes) + jj), a);
+#pragma unroll
+                            for (int e = 0; e < EPV; e += 2)
+                                fma2(y[e], y[e + 1], cr[rr], cr[rr], a[e], a[e + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e)
+                        py[jj * EPV + e] = y[e];
+                }
+            }
+        }
+        ++grp_counter;
+    }
+    if (tid == 0) {
+        PartStat ps;
+        ps.h = h_loc;
+        ps.maxviol = (double)mv;
+        ps.maxnorm = (double)mn;
+        ps.maxb = (double)mb;
+        p.part_stat[b] = ps;
+    }
+}
+
 // ---------------------------------------------------- reduce and update ----
 //
 // Block = 256 threads = 8 groups x 32 columns.  Group q sums partial rows
@@ -1081,6 +1249,8 @@ static const void *map_fn_any(int storage, int vpt, bool guard)
 
 cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
 {
+    if (vpt == 0)
+        return cudaSuccess;  // long rows: static shared memory only
     const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)
         return cudaErrorInvalidValue;
@@ -1090,6 +1260,16 @@ cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
 cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers, size_t smem, cudaStream_t s,
                        const MapArgs &a)
 {
+    if (vpt == 0) {
+        switch (storage) {
+        case NSLI_F64: map_long_kernel<NSLI_F64><<<grid, kLongThreads, 0, s>>>(a); break;
+        case NSLI_F32: map_long_kernel<NSLI_F32><<<grid, kLongThreads, 0, s>>>(a); break;
+        case NSLI_BF16: map_long_kernel<NSLI_BF16><<<grid, kLongThreads, 0, s>>>(a); break;
+        case NSLI_FP8E4M3: map_long_kernel<NSLI_FP8E4M3><<<grid, kLongThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)
         return cudaErrorInvalidValue;
