@@ -113,6 +113,10 @@ def _load():
         lib.oracle_quantize_bf16.restype = None
         lib.oracle_quantize_e4m3_rows.argtypes = [i64, i64, P, P, P]
         lib.oracle_quantize_e4m3_rows.restype = None
+        lib.oracle_map_reduce_csr.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_map_reduce_csr.restype = None
+        lib.oracle_norms2_csr.argtypes = [i64, P, P, P]
+        lib.oracle_norms2_csr.restype = i64
         _lib = lib
         return lib
 
@@ -168,6 +172,33 @@ def map_reduce(A, b, n2, x) -> dict:
     fn(m, n, _ptr(A), _ptr(b), _ptr(n2), _ptr(x), _ptr(y),
                               ctypes.byref(h), ctypes.byref(mv), ctypes.byref(mn),
                               ctypes.byref(mb), _ptr(r))
+    return {"y": y, "h": int(h.value), "maxviol": mv.value, "maxnorm": mn.value,
+            "maxb": mb.value, "r": r}
+
+
+def norms2_csr(rp, val) -> tuple[np.ndarray, int]:
+    """||a_i||^2 per compressed row in FP64 and the number of zero rows."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    val = _f64(val)
+    m = rp.size - 1
+    n2 = np.empty(m, np.float64)
+    zero = _load().oracle_norms2_csr(m, _ptr(rp), _ptr(val), _ptr(n2))
+    return n2, int(zero)
+
+
+def map_reduce_csr(rp, ci, val, n, b, n2, x) -> dict:
+    """map_reduce for A in compressed-row form (row_ptr, col_idx, val)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    val, b, n2, x = _f64(val), _f64(b), _f64(n2), _f64(x)
+    m = rp.size - 1
+    y = np.empty(n, np.float64)
+    r = np.empty(m, np.float64)
+    h = ctypes.c_int64()
+    mv, mn, mb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _load().oracle_map_reduce_csr(m, int(n), _ptr(rp), _ptr(ci), _ptr(val), _ptr(b), _ptr(n2),
+                                  _ptr(x), _ptr(y), ctypes.byref(h), ctypes.byref(mv),
+                                  ctypes.byref(mn), ctypes.byref(mb), _ptr(r))
     return {"y": y, "h": int(h.value), "maxviol": mv.value, "maxnorm": mn.value,
             "maxb": mb.value, "r": r}
 

@@ -196,6 +196,64 @@ int64_t oracle_norms2_f32(int64_t m, int64_t n, const float *A, double *n2)
     return zero_rows;
 }
 
+/* The same Map and Reduce for A in compressed-row form: row i holds the
+ * entries val[e] at columns ci[e], e = rp[i] .. rp[i+1]-1, columns
+ * ascending.  Each sum runs over the stored entries of a row in column
+ * order, which is the order of oracle_map_reduce with the zero entries left
+ * out (adding a zero product changes no sum). */
+void oracle_map_reduce_csr(int64_t m, int64_t n, const int64_t *rp,
+                           const int32_t *ci, const double *val,
+                           const double *b, const double *n2, const double *x,
+                           double *y, int64_t *h, double *maxviol,
+                           double *maxnorm, double *maxb, double *r)
+{
+    for (int64_t j = 0; j < n; ++j)
+        y[j] = 0.0;
+    int64_t count = 0;
+    double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double dot = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            dot = dot + val[e] * x[ci[e]];
+        double ri = dot - b[i];
+        if (r != NULL)
+            r[i] = ri;
+        if (ri > mv)
+            mv = ri;
+        double rn = ri / sqrt(n2[i]);
+        if (rn > mn)
+            mn = rn;
+        if (fabs(b[i]) > mb)
+            mb = fabs(b[i]);
+        if (ri > 0.0) {
+            double c = ri / n2[i];
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+                y[ci[e]] = y[ci[e]] + c * val[e];
+            count = count + 1;
+        }
+    }
+    *h = count;
+    *maxviol = mv;
+    *maxnorm = mn;
+    *maxb = mb;
+}
+
+/* ||a_i||^2 of compressed rows; returns the number of zero rows. */
+int64_t oracle_norms2_csr(int64_t m, const int64_t *rp, const double *val,
+                          double *n2)
+{
+    int64_t zero_rows = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            s = s + val[e] * val[e];
+        n2[i] = s;
+        if (s == 0.0)
+            zero_rows = zero_rows + 1;
+    }
+    return zero_rows;
+}
+
 static int stop_test_passes(int stop, double eps, double maxviol,
                             double maxnorm, double maxb)
 {

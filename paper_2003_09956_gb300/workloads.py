@@ -20,6 +20,9 @@ did not survive; these stand in for it):
   format; b0 and Av are then computed from the rounded A.
 * ``small_polytope(n, m)``: a small random system around a known interior
   point, for brute-force checks.
+* ``sparse_system(m, n, k)``: the dense system's recipe with k non-zeros per
+  row at random distinct columns (compressed-row form), or row lengths given
+  per row; ``model_system_csr(n)``: the model system in compressed-row form.
 
 Large matrices are drawn in fixed row chunks, each from its own
 ``SeedSequence`` child, so the bytes do not depend on the thread count.
@@ -174,3 +177,84 @@ def small_polytope(n: int, m: int, seed: int, spread: float = 3.0) -> dict:
     x0 = z + g.normal(0.0, spread, n) * 3.0
     return {"A": A, "b0": b0, "Av": None, "x0": x0, "z": z, "m": A.shape[0],
             "n": n, "seed": seed}
+
+
+def _csr_rows_dot(rp: np.ndarray, ci: np.ndarray, val: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """sum_e val[e] v[ci[e]] per row, binary64 (input construction only)."""
+    m = rp.size - 1
+    prod = val * v[ci]
+    out = np.add.reduceat(prod, rp[:-1]) if prod.size else np.zeros(m)
+    out[rp[:-1] == rp[1:]] = 0.0
+    return out
+
+
+def sparse_system(m: int, n: int, k: int, seed: int, x0_std: float = 5.0,
+                  lengths: np.ndarray | None = None) -> dict:
+    """Sparse non-stationary random system in compressed-row form.
+
+    Row i has k non-zeros (or ``lengths[i]``) at distinct columns, ascending;
+    the entries are N(0, 1) rounded to binary32.  As for ``dense_system``:
+    z ~ U(-1, 1)^n, b0 = A z + U(0.1, 1.0), v = g / ||g||, Av = A v (binary64),
+    x0 ~ N(0, x0_std^2 I) rounded to binary32.  With a fixed k the columns of
+    a row are a sorted sample with replacement from [0, n - k] plus 0..k-1
+    (distinct by construction); with ``lengths`` each row is a uniform
+    sample without replacement."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    if lengths is None:
+        if not 1 <= k <= n:
+            raise ValueError("need 1 <= k <= n")
+        rp = np.arange(0, m * k + 1, k, dtype=np.int64)
+        ci = np.empty(m * k, np.int32)
+        val = np.empty(m * k, np.float64)
+        step = 1 << 18
+        for r0 in range(0, m, step):
+            r1 = min(m, r0 + step)
+            c = g.integers(0, n - k + 1, size=(r1 - r0, k), dtype=np.int64)
+            c.sort(axis=1)
+            c += np.arange(k, dtype=np.int64)
+            ci[r0 * k:r1 * k] = c.reshape(-1)
+            val[r0 * k:r1 * k] = g.standard_normal((r1 - r0) * k, dtype=np.float32)
+    else:
+        lengths = np.asarray(lengths, dtype=np.int64)
+        if lengths.shape != (m,) or lengths.min() < 1 or lengths.max() > n:
+            raise ValueError("lengths must hold m values in [1, n]")
+        rp = np.zeros(m + 1, np.int64)
+        np.cumsum(lengths, out=rp[1:])
+        ci = np.empty(int(rp[-1]), np.int32)
+        for i in range(m):
+            ci[rp[i]:rp[i + 1]] = np.sort(g.choice(n, int(lengths[i]), replace=False))
+        val = g.standard_normal(ci.size, dtype=np.float32).astype(np.float64)
+    z = g.uniform(-1.0, 1.0, n)
+    slack = g.uniform(0.1, 1.0, m)
+    dirn = g.standard_normal(n)
+    v = dirn / np.sqrt(np.sum(dirn * dirn))
+    x0 = g.normal(0.0, x0_std, n).astype(np.float32).astype(np.float64)
+    b0 = _csr_rows_dot(rp, ci, val, z) + slack
+    Av = _csr_rows_dot(rp, ci, val, v)
+    return {"rp": rp, "ci": ci, "val": val, "b0": b0, "Av": Av, "x0": x0, "z": z, "v": v,
+            "m": m, "n": n, "nnz": int(ci.size), "seed": seed}
+
+
+def model_system_csr(n: int, seed: int) -> dict:
+    """``model_system(n)`` in compressed-row form (3n non-zeros)."""
+    m = 2 * n + 1
+    idx = np.arange(n, dtype=np.int64)
+    rp = np.concatenate([np.arange(0, 2 * n + 1, dtype=np.int64), [3 * n]])
+    ci = np.concatenate([idx, idx, idx]).astype(np.int32)
+    val = np.concatenate([-np.ones(n), np.ones(n), np.ones(n)])
+    b0 = np.zeros(m, np.float64)
+    b0[n:2 * n] = 200.0
+    b0[2 * n] = 200.0 * (n - 1) + 100.0
+    g = np.random.Generator(np.random.PCG64(seed))
+    x0 = g.uniform(300.0, 400.0, n)
+    return {"rp": rp, "ci": ci, "val": val, "b0": b0, "Av": None, "x0": x0,
+            "z": np.full(n, 100.0), "m": m, "n": n, "nnz": 3 * n, "seed": seed}
+
+
+def csr_to_dense(rp: np.ndarray, ci: np.ndarray, val: np.ndarray, n: int) -> np.ndarray:
+    """Dense binary64 copy of a compressed-row matrix (small sizes)."""
+    m = rp.size - 1
+    A = np.zeros((m, n), np.float64)
+    rows = np.repeat(np.arange(m), np.diff(rp))
+    A[rows, ci] = val
+    return A

@@ -406,3 +406,42 @@ def test_only_strictly_violated_rows_count():
     assert mr["h"] == 1
     np.testing.assert_array_equal(mr["y"], [2.0, 0.0])
     assert mr["maxviol"] == 2.0
+
+
+# ---- compressed-row (sparse) form ---------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_csr_map_reduce_equals_dense_oracle_bitwise(seed):
+    """Leaving out the zero entries changes no sum (a zero product adds
+    nothing), so the compressed-row Map/Reduce is the dense one bit for bit
+    on the same matrix, including ragged rows and unused columns."""
+    from paper_2003_09956_gb300 import workloads
+    g = np.random.default_rng(seed)
+    m, n = 300, 90
+    lengths = g.integers(1, 40, m)
+    p = workloads.sparse_system(m, n, 0, seed=seed, lengths=lengths)
+    A = workloads.csr_to_dense(p["rp"], p["ci"], p["val"], n)
+    n2d, zd = oracle.norms2(A)
+    n2s, zs = oracle.norms2_csr(p["rp"], p["val"])
+    np.testing.assert_array_equal(n2s, n2d)
+    assert zs == zd == 0
+    b = oracle.tick_b(p["b0"], p["Av"], 0.3, 5)
+    x = g.normal(0.0, 2.0, n)
+    d = oracle.map_reduce(A, b, n2d, x)
+    c = oracle.map_reduce_csr(p["rp"], p["ci"], p["val"], n, b, n2s, x)
+    np.testing.assert_array_equal(c["y"], d["y"])
+    np.testing.assert_array_equal(c["r"], d["r"])
+    assert (c["h"], c["maxviol"], c["maxnorm"], c["maxb"]) == \
+        (d["h"], d["maxviol"], d["maxnorm"], d["maxb"])
+    assert 0 < c["h"] < m
+
+
+def test_csr_model_system_is_the_model_system():
+    from paper_2003_09956_gb300 import workloads
+    p = workloads.model_system_csr(7, seed=4)
+    q = workloads.model_system(7, seed=4)
+    np.testing.assert_array_equal(workloads.csr_to_dense(p["rp"], p["ci"], p["val"], 7), q["A"])
+    np.testing.assert_array_equal(p["b0"], q["b0"])
+    n2, zero = oracle.norms2_csr(p["rp"], p["val"])
+    np.testing.assert_array_equal(n2, np.r_[np.ones(14), 7.0])
+    assert zero == 0
