@@ -132,6 +132,33 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage,
                 const double *norms2, const double *Av, const double *x0,
                 void *stream);
 
+/* Create a solver for a SPARSE m x n system A x <= b0 + k rho Av (the same
+ * method, Sections 2, 3 and 5; the paper's test system, Section 5, has a
+ * few non-zeros per row).  A is given in compressed-row form:
+ *   row_ptr   host or device, m + 1 int64 offsets, row_ptr[0] = 0,
+ *             non-decreasing, row_ptr[m] = nnz;
+ *   col_idx   host or device, nnz int32 column indices, strictly increasing
+ *             within each row (no duplicates), each in [0, n);
+ *   val       host or device, nnz doubles, the entries in the same order.
+ *   storage   NSLI_F64 or NSLI_F32 (entries rounded to nearest even);
+ *             others give NSLI_ERR_UNSUPPORTED.
+ * b0, norms2, Av, x0 and stream as for nsli_create.  The library keeps A
+ * twice on the device, by rows (for the residuals) and by columns (so every
+ * y_j is summed in one fixed order, rows ascending: results are bitwise
+ * reproducible), about 2 nnz (4 + element size) bytes.  The structure is
+ * copied and checked on the host; nothing is retained.  Every other call
+ * on the handle works as for a dense one, except nsli_test_inject_timeout
+ * (NSLI_ERR_UNSUPPORTED); a ModAP iteration is three kernel launches
+ * instead of two.  Errors: NSLI_ERR_ARG (sizes < 1, NULL required pointer,
+ * malformed offsets or indices), NSLI_ERR_UNSUPPORTED (storage, m or n
+ * >= 2^31), NSLI_ERR_ZERO_ROW (an empty or all-zero row),
+ * NSLI_ERR_NONFINITE, NSLI_ERR_OOM, NSLI_ERR_CUDA.  On error *out is NULL
+ * and nothing is leaked. */
+int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage,
+                    int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,
+                    const double *val, const double *b0, const double *norms2,
+                    const double *Av, const double *x0, void *stream);
+
 /* Replace b0 (host or device, m doubles; NULL keeps the current b0) and set
  * the tick k used by the next iteration (tick < 0 keeps the current tick).
  * Section 5: the data update step of each iteration. */

@@ -11,8 +11,9 @@ the other way the box would sweep over x0 and every rate would count as
 caught.  For the dense random system v is its own random unit direction.
 
 Storage: binary64 for the systems held on the host (Algorithm 1's rate is
-eps-sized, below binary32 resolution), bf16 for the large model systems
-(their entries 0 and +-1 are exact; only ModAP runs there).
+eps-sized, below binary32 resolution) and for the model systems in
+compressed-row form, bf16 for the large dense model systems (their entries
+0 and +-1 are exact; only ModAP runs there).
 
 The catch-up rate of a rule (Algorithm 1 with relaxation lambda, Eq. 8, or
 ModAP with step length lambda, Eq. 12) is the supremum of the rates rho for
@@ -71,6 +72,18 @@ def model_system_translated_device(n: int, seed: int = 0, device=None) -> dict:
     x0 = g.uniform(300.0, 400.0, n)
     return {"A": A, "b0": b0, "Av": Av, "x0": x0, "m": m, "n": n, "seed": seed,
             "v_norm": math.sqrt(n)}
+
+
+def model_system_translated_csr(n: int, seed: int = 0) -> dict:
+    """The model system in compressed-row form (3n non-zeros), same v."""
+    p = workloads.model_system_csr(n, seed)
+    Av = np.empty(p["m"], np.float64)
+    Av[:n] = 1.0
+    Av[n:2 * n] = -1.0
+    Av[2 * n] = -float(n)
+    p["Av"] = Av
+    p["v_norm"] = math.sqrt(n)
+    return p
 
 
 def dense_system_translated(m: int, n: int, seed: int = 0) -> dict:
@@ -136,7 +149,11 @@ class GpuTrials:
                  storage: str = "f64", block_iters: int = 64):
         self.p, self.rule, self.lam = p, rule, lam
         self.eps, self.max_iter, self.block_iters = eps, max_iter, block_iters
-        self.solver = nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage)
+        if "rp" in p:
+            self.solver = nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"],
+                                            Av=p["Av"], storage=storage)
+        else:
+            self.solver = nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage)
         self.last = None
 
     def close(self):
@@ -210,6 +227,8 @@ def main():
     ap.add_argument("--model-n", type=int, nargs="*", default=[256, 4096])
     ap.add_argument("--model-device-n", type=int, nargs="*", default=[],
                     help="model systems built in device memory (large n, bf16 storage)")
+    ap.add_argument("--model-sparse-n", type=int, nargs="*", default=[],
+                    help="model systems in compressed-row form (binary64)")
     ap.add_argument("--dense", nargs="*", default=[], help="MxN dense random systems")
     ap.add_argument("--lam-per-coordinate", type=float, nargs="+", default=[0.1, 1.0, 10.0],
                     help="ModAP step lengths, lambda = c * sqrt(n)")
@@ -230,6 +249,10 @@ def main():
         p = model_system_translated_device(n, device=torch.device("cuda", torch.cuda.current_device()))
         p["name"] = f"model-{n}"
         systems.append((p, "bf16"))
+    for n in args.model_sparse_n:
+        p = model_system_translated_csr(n)
+        p["name"] = f"model-{n}-csr"
+        systems.append((p, "f64"))
     for spec in args.dense:
         m, n = (int(v) for v in spec.lower().split("x"))
         p = dense_system_translated(m, n)

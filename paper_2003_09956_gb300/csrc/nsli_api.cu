@@ -44,8 +44,17 @@ struct nsli_solver {
     VerOut *ver_host = nullptr;   // pinned
     int *flags_host = nullptr;    // pinned
 
+    // sparse A (nsli_create_csr): CSR + CSC copies, see nsli_sparse.cu
+    bool sparse = false;
+    long long nnz = 0;
+    long long *rp = nullptr, *cp = nullptr;
+    int *ci = nullptr, *ri = nullptr, *heavy_rows = nullptr, *heavy_cols = nullptr;
+    void *va = nullptr, *vc = nullptr, *coef = nullptr;
+    SparseArgs sp{};
+
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
+    int graph_rule = -1;
     long long launches = 0;
 
     nsli_result last_check{};
@@ -96,7 +105,8 @@ void free_all(nsli_solver *h)
         cudaGraphExecDestroy(h->graph);
     void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
                    h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags,
-                   (h->x64 != h->x) ? (void *)h->x64 : nullptr};
+                   (h->x64 != h->x) ? (void *)h->x64 : nullptr,
+                   h->rp, h->cp, h->ci, h->ri, h->heavy_rows, h->heavy_cols, h->va, h->vc, h->coef};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -208,17 +218,35 @@ ReduceArgs reduce_args(nsli_solver *h)
     return a;
 }
 
-cudaError_t launch_iteration(nsli_solver *h)
+// kernels per iteration: Map + Reduce/step; a sparse A adds the ModAP step
+int launches_per_iteration(const nsli_solver *h, int rule)
 {
+    return (h->sparse && rule == NSLI_RULE_MODAP) ? 3 : 2;
+}
+
+cudaError_t launch_iteration(nsli_solver *h, int rule)
+{
+    if (h->sparse) {
+        const bool f64 = h->storage == NSLI_F64;
+        cudaError_t e = sparse_row_launch(f64, h->stream, h->sp);
+        if (e == cudaSuccess)
+            e = sparse_col_launch(f64, h->stream, h->sp);
+        if (e == cudaSuccess && rule == NSLI_RULE_MODAP)
+            e = sparse_step_launch(f64, h->stream, h->sp);
+        return e;
+    }
     cudaError_t e = map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, map_args(h));
     if (e != cudaSuccess)
         return e;
     return reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
 }
 
-int ensure_graph(nsli_solver *h, int iters)
+int ensure_graph(nsli_solver *h, int iters, int rule)
 {
-    if (h->graph && h->graph_iters == iters)
+    // the dense kernels read the rule at run time; the sparse ModAP graph
+    // holds one more kernel per iteration
+    const int key = h->sparse ? rule : -1;
+    if (h->graph && h->graph_iters == iters && h->graph_rule == key)
         return NSLI_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -227,7 +255,7 @@ int ensure_graph(nsli_solver *h, int iters)
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < iters && err == cudaSuccess; ++i)
-        err = launch_iteration(h);
+        err = launch_iteration(h, rule);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (err != cudaSuccess) {
@@ -240,6 +268,7 @@ int ensure_graph(nsli_solver *h, int iters)
     cudaGraphDestroy(g);
     CK(e3, "instantiate iteration graph");
     h->graph_iters = iters;
+    h->graph_rule = key;
     return NSLI_OK;
 }
 
@@ -299,7 +328,10 @@ int run_verify(nsli_solver *h)
     a.m = h->m;
     a.nv = h->nv;
     const int grid = std::max(1, std::min<int>(h->num_sms * 8, (int)((h->m + 7) / 8)));
-    CK(verify_launch(h->storage, grid, h->stream, a), "launch binary64 check");
+    if (h->sparse)
+        CK(sparse_verify_launch(h->storage == NSLI_F64, grid, h->stream, h->sp, a), "launch binary64 check");
+    else
+        CK(verify_launch(h->storage, grid, h->stream, a), "launch binary64 check");
     h->launches += 1;
     CK(cudaMemcpyAsync(h->ver_host, h->ver, sizeof(VerOut), cudaMemcpyDeviceToHost, h->stream), "read check");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
@@ -535,6 +567,243 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
     return NSLI_OK;
 }
 
+int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col_idx, const double *val, const double *b0, const double *norms2,
+                    const double *Av, const double *x0, void *stream)
+{
+    if (!out)
+        return NSLI_ERR_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || nnz < 1 || !row_ptr || !col_idx || !val || !b0 || !x0)
+        return NSLI_ERR_ARG;
+    if (storage != NSLI_F64 && storage != NSLI_F32)
+        return NSLI_ERR_UNSUPPORTED;
+    if (m >= (1ll << 31) || n >= (1ll << 31) || nnz > (1ll << 40))
+        return NSLI_ERR_UNSUPPORTED;
+
+    nsli_solver *h = new nsli_solver();
+    h->sparse = true;
+    h->storage = storage;
+    h->m = m;
+    h->n = n;
+    h->ld = n;
+    h->nnz = nnz;
+    h->elem_bytes = storage == NSLI_F64 ? 8 : 4;
+    auto fail = [&](int code) {
+        free_all(h);
+        delete h;
+        return code;
+    };
+#define CKC(call, what)                                                                                      \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return fail(cuda_err(h, e_, what));                                                              \
+    } while (0)
+
+    CKC(cudaGetDevice(&h->device), "get device");
+    CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+
+    // host copies of the structure (the inputs may be device memory); the
+    // column-major copy is built by a stable counting sort, so the rows of
+    // every column stay ascending
+    std::vector<long long> rp((size_t)m + 1);
+    std::vector<int> ci((size_t)nnz);
+    std::vector<double> va((size_t)nnz);
+    CKC(cudaMemcpy(rp.data(), row_ptr, (size_t)(m + 1) * 8, cudaMemcpyDefault), "copy row offsets");
+    CKC(cudaMemcpy(ci.data(), col_idx, (size_t)nnz * 4, cudaMemcpyDefault), "copy column indices");
+    CKC(cudaMemcpy(va.data(), val, (size_t)nnz * 8, cudaMemcpyDefault), "copy values");
+    if (rp[0] != 0 || rp[m] != nnz)
+        return fail(set_err(h, NSLI_ERR_ARG, "row offsets must start at 0 and end at nnz"));
+    for (long long i = 0; i < m; ++i) {
+        if (rp[i + 1] < rp[i])
+            return fail(set_err(h, NSLI_ERR_ARG, "row offsets must not decrease"));
+        for (long long e = rp[i]; e < rp[i + 1]; ++e) {
+            if (ci[e] < 0 || ci[e] >= n)
+                return fail(set_err(h, NSLI_ERR_ARG, "column index out of range"));
+            if (e > rp[i] && ci[e] <= ci[e - 1])
+                return fail(set_err(h, NSLI_ERR_ARG, "column indices must increase strictly within a row"));
+            if (!std::isfinite(va[e]))
+                return fail(set_err(h, NSLI_ERR_NONFINITE, "NaN or Inf in the input"));
+        }
+    }
+    std::vector<long long> cp((size_t)n + 1, 0);
+    for (long long e = 0; e < nnz; ++e)
+        cp[(size_t)ci[e] + 1] += 1;
+    for (long long j = 0; j < n; ++j)
+        cp[j + 1] += cp[j];
+    std::vector<long long> fill(cp.begin(), cp.end() - 1);
+    std::vector<int> ri((size_t)nnz);
+    std::vector<double> vcol((size_t)nnz);
+    for (long long i = 0; i < m; ++i)
+        for (long long e = rp[i]; e < rp[i + 1]; ++e) {
+            const long long k = fill[ci[e]]++;
+            ri[k] = (int)i;
+            vcol[k] = va[e];
+        }
+
+    // lanes per row / column from the median length (a few very long rows or
+    // columns do not set it); those longer than 256 passes of that width get
+    // a CTA each
+    auto median_len = [](const std::vector<long long> &off) {
+        std::vector<long long> len(off.size() - 1);
+        for (size_t i = 0; i + 1 < off.size(); ++i)
+            len[i] = off[i + 1] - off[i];
+        std::nth_element(len.begin(), len.begin() + len.size() / 2, len.end());
+        return (double)len[len.size() / 2];
+    };
+    auto pick_w = [](double typical) {
+        int w = 1;
+        while (w < 32 && w < typical / 2.0)
+            w *= 2;
+        return w;
+    };
+    SparseArgs &sp = h->sp;
+    sp = SparseArgs{};
+    sp.m = m;
+    sp.n = n;
+    sp.w_row = pick_w(median_len(rp));
+    sp.w_col = pick_w(median_len(cp));
+    sp.heavy_thr_row = std::max<long long>(512, 256ll * sp.w_row);
+    sp.heavy_thr_col = std::max<long long>(512, 256ll * sp.w_col);
+    std::vector<int> hr, hc;
+    for (long long i = 0; i < m; ++i)
+        if (rp[i + 1] - rp[i] > sp.heavy_thr_row)
+            hr.push_back((int)i);
+    for (long long j = 0; j < n; ++j)
+        if (cp[j + 1] - cp[j] > sp.heavy_thr_col)
+            hc.push_back((int)j);
+    sp.n_heavy_rows = (int)hr.size();
+    sp.n_heavy_cols = (int)hc.size();
+    auto split = [&](long long items, int w, int *ctas, long long *per) {
+        const long long groups = 256 / w;
+        long long c = (items + groups * 4 - 1) / (groups * 4);
+        c = std::max<long long>(1, std::min<long long>(c, (long long)h->num_sms * 8));
+        *per = (items + c - 1) / c;
+        *ctas = (int)((items + *per - 1) / *per);
+    };
+    split(m, sp.w_row, &sp.row_light_ctas, &sp.light_rows_per_cta);
+    split(n, sp.w_col, &sp.col_light_ctas, &sp.light_cols_per_cta);
+    sp.step_ctas = (int)std::max<long long>(1, std::min<long long>((n + 1023) / 1024, (long long)h->num_sms * 4));
+    const long long g_row = sp.n_heavy_rows + sp.row_light_ctas;
+    const long long g_col = std::max<long long>(sp.n_heavy_cols + sp.col_light_ctas, sp.step_ctas);
+    h->G = (int)g_row;
+
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CKC(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "create stream");
+        h->own_stream = true;
+    }
+    cudaStream_t s = h->stream;
+    const size_t eb = (size_t)h->elem_bytes;
+    CKC(cudaMalloc((void **)&h->rp, (size_t)(m + 1) * 8), "allocate row offsets");
+    CKC(cudaMalloc((void **)&h->ci, (size_t)nnz * 4), "allocate column indices");
+    CKC(cudaMalloc(&h->va, (size_t)nnz * eb), "allocate row values");
+    CKC(cudaMalloc((void **)&h->cp, (size_t)(n + 1) * 8), "allocate column offsets");
+    CKC(cudaMalloc((void **)&h->ri, (size_t)nnz * 4), "allocate row indices");
+    CKC(cudaMalloc(&h->vc, (size_t)nnz * eb), "allocate column values");
+    if (!hr.empty())
+        CKC(cudaMalloc((void **)&h->heavy_rows, hr.size() * 4), "allocate heavy rows");
+    if (!hc.empty())
+        CKC(cudaMalloc((void **)&h->heavy_cols, hc.size() * 4), "allocate heavy columns");
+    CKC(cudaMalloc(&h->coef, (size_t)m * eb), "allocate slice coefficients");
+    CKC(cudaMalloc(&h->meta, (size_t)m * 32), "allocate row records");
+    CKC(cudaMalloc((void **)&h->b0_64, (size_t)m * 8), "allocate b0");
+    CKC(cudaMalloc((void **)&h->av_64, (size_t)m * 8), "allocate Av");
+    CKC(cudaMalloc((void **)&h->n2_64, (size_t)m * 8), "allocate norms");
+    CKC(cudaMalloc(&h->x, (size_t)n * eb), "allocate x");
+    if (storage == NSLI_F64)
+        h->x64 = static_cast<double *>(h->x);
+    else
+        CKC(cudaMalloc((void **)&h->x64, (size_t)n * 8), "allocate binary64 x");
+    CKC(cudaMalloc((void **)&h->part_stat, (size_t)g_row * sizeof(PartStat)), "allocate partial stats");
+    CKC(cudaMalloc((void **)&h->part_dx, (size_t)g_col * 8), "allocate step partials");
+    CKC(cudaMalloc((void **)&h->ybuf, (size_t)n * 8), "allocate y");
+    CKC(cudaMalloc((void **)&h->dtmp, (size_t)std::max<long long>(m, n) * 8), "allocate staging");
+    CKC(cudaMalloc((void **)&h->st, sizeof(DevState)), "allocate state");
+    CKC(cudaMalloc((void **)&h->ver, sizeof(VerOut)), "allocate check");
+    CKC(cudaMalloc((void **)&h->flags, sizeof(int)), "allocate flags");
+    CKC(cudaMallocHost((void **)&h->st_host, sizeof(DevState)), "allocate pinned state");
+    CKC(cudaMallocHost((void **)&h->ver_host, sizeof(VerOut)), "allocate pinned check");
+    CKC(cudaMallocHost((void **)&h->flags_host, sizeof(int)), "allocate pinned flags");
+
+    // values in the storage type (binary32: rounded to nearest, ties to even)
+    std::vector<float> va32, vc32;
+    const void *va_src = va.data(), *vc_src = vcol.data();
+    if (storage == NSLI_F32) {
+        va32.assign(va.begin(), va.end());
+        vc32.assign(vcol.begin(), vcol.end());
+        va_src = va32.data();
+        vc_src = vc32.data();
+    }
+    CKC(cudaMemcpyAsync(h->rp, rp.data(), (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, s), "upload row offsets");
+    CKC(cudaMemcpyAsync(h->ci, ci.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s), "upload column indices");
+    CKC(cudaMemcpyAsync(h->va, va_src, (size_t)nnz * eb, cudaMemcpyHostToDevice, s), "upload row values");
+    CKC(cudaMemcpyAsync(h->cp, cp.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s), "upload column offsets");
+    CKC(cudaMemcpyAsync(h->ri, ri.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s), "upload row indices");
+    CKC(cudaMemcpyAsync(h->vc, vc_src, (size_t)nnz * eb, cudaMemcpyHostToDevice, s), "upload column values");
+    if (!hr.empty())
+        CKC(cudaMemcpyAsync(h->heavy_rows, hr.data(), hr.size() * 4, cudaMemcpyHostToDevice, s), "upload heavy rows");
+    if (!hc.empty())
+        CKC(cudaMemcpyAsync(h->heavy_cols, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, s),
+            "upload heavy columns");
+
+    sp.rp = h->rp;
+    sp.ci = h->ci;
+    sp.va = h->va;
+    sp.cp = h->cp;
+    sp.ri = h->ri;
+    sp.vc = h->vc;
+    sp.meta = h->meta;
+    sp.heavy_rows = h->heavy_rows;
+    sp.heavy_cols = h->heavy_cols;
+    sp.coef = h->coef;
+    sp.x = h->x;
+    sp.x64 = h->x64;
+    sp.ybuf = h->ybuf;
+    sp.part_stat = h->part_stat;
+    sp.part_dx = h->part_dx;
+    sp.st = h->st;
+    sp.ignore_done = 0;
+    sp.mode = 0;
+
+    CKC(cudaMemsetAsync(h->st, 0, sizeof(DevState), s), "clear state");
+    CKC(cudaMemsetAsync(h->flags, 0, sizeof(int), s), "clear flags");
+    CKC(cudaMemsetAsync(h->ybuf, 0, (size_t)n * 8, s), "clear y");
+    CKC(cudaMemsetAsync(h->coef, 0, (size_t)m * eb, s), "clear coefficients");
+    CKC(cudaMemcpyAsync(h->b0_64, b0, (size_t)m * 8, cudaMemcpyDefault, s), "copy b0");
+    if (Av)
+        CKC(cudaMemcpyAsync(h->av_64, Av, (size_t)m * 8, cudaMemcpyDefault, s), "copy Av");
+    else
+        CKC(cudaMemsetAsync(h->av_64, 0, (size_t)m * 8, s), "clear Av");
+    CKC(check_finite_launch(s, h->b0_64, m, h->flags), "check b0");
+    CKC(check_finite_launch(s, h->av_64, m, h->flags), "check Av");
+    CKC(cudaMemcpyAsync(h->dtmp, x0, (size_t)n * 8, cudaMemcpyDefault, s), "copy x0");
+    CKC(x_from_f64_launch(storage == NSLI_F64, s, h->dtmp, h->x64, h->x, n, n, h->flags), "convert x0");
+    const int ngrid = (int)std::max<long long>(1, std::min<long long>((long long)h->num_sms * 8, (m + 7) / 8));
+    CKC(sparse_norms_launch(storage == NSLI_F64, ngrid, s, sp, h->n2_64, h->flags), "row norms");
+    if (norms2)
+        CKC(cudaMemcpyAsync(h->n2_64, norms2, (size_t)m * 8, cudaMemcpyDefault, s), "copy norms");
+    MetaArgs ma;
+    ma.meta = h->meta;
+    ma.b0_64 = h->b0_64;
+    ma.av_64 = h->av_64;
+    ma.n2_64 = h->n2_64;
+    ma.scale = nullptr;
+    ma.m = m;
+    ma.flags = h->flags;
+    CKC(meta_launch(storage == NSLI_F64, s, ma), "row records");
+    h->launches += 5;
+    CKC(cudaStreamSynchronize(s), "synchronize");
+    int rc = read_flags(h);
+    if (rc != NSLI_OK)
+        return fail(rc);
+#undef CKC
+    *out = h;
+    return NSLI_OK;
+}
+
 void nsli_destroy(nsli_handle h)
 {
     if (!h)
@@ -594,17 +863,18 @@ int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)
     const int B = p->block_iters > 0 ? p->block_iters : 32;
     const long long full = n_iter / B;
     const long long rem = n_iter % B;
+    const int per = launches_per_iteration(h, p->rule);
     if (full > 0) {
-        if ((rc = ensure_graph(h, B)) != NSLI_OK)
+        if ((rc = ensure_graph(h, B, p->rule)) != NSLI_OK)
             return rc;
         for (long long i = 0; i < full; ++i) {
             CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
-            h->launches += 2ll * B;
+            h->launches += (long long)per * B;
         }
     }
     for (long long i = 0; i < rem; ++i) {
-        CK(launch_iteration(h), "launch iteration");
-        h->launches += 2;
+        CK(launch_iteration(h, p->rule), "launch iteration");
+        h->launches += per;
     }
     return NSLI_OK;
 }
@@ -631,13 +901,23 @@ int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter, doub
         const int cnt = (int)std::min<long long>(batch, n_iter - done);
         for (int i = 0; i < cnt && err == cudaSuccess; ++i) {
             cudaEventRecord(ev[3 * i], h->stream);
-            err = map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, map_args(h));
+            if (h->sparse)
+                err = sparse_row_launch(h->storage == NSLI_F64, h->stream, h->sp);
+            else
+                err = map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream,
+                                 map_args(h));
             if (err != cudaSuccess)
                 break;
             cudaEventRecord(ev[3 * i + 1], h->stream);
-            err = reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
+            if (h->sparse) {
+                err = sparse_col_launch(h->storage == NSLI_F64, h->stream, h->sp);
+                if (err == cudaSuccess && p->rule == NSLI_RULE_MODAP)
+                    err = sparse_step_launch(h->storage == NSLI_F64, h->stream, h->sp);
+            } else {
+                err = reduce_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h));
+            }
             cudaEventRecord(ev[3 * i + 2], h->stream);
-            h->launches += 2;
+            h->launches += launches_per_iteration(h, p->rule);
         }
         if (err == cudaSuccess)
             err = cudaStreamSynchronize(h->stream);
@@ -666,8 +946,9 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     if ((rc = begin_run(h, p, p->stop, p->max_iter)) != NSLI_OK)
         return rc;
     const int B = p->block_iters > 0 ? p->block_iters : 32;
-    if ((rc = ensure_graph(h, B)) != NSLI_OK)
+    if ((rc = ensure_graph(h, B, p->rule)) != NSLI_OK)
         return rc;
+    const int per = launches_per_iteration(h, p->rule);
     int status = NSLI_NOT_CONVERGED;
     // every block either makes B updates or ends the run; a rejected
     // candidate forces one update, so this bound is never reached
@@ -675,7 +956,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     bool finished = false;
     for (long long blk = 0; blk < max_blocks && !finished; ++blk) {
         CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
-        h->launches += 2ll * B;
+        h->launches += (long long)per * B;
         if ((rc = read_state(h)) != NSLI_OK)
             return rc;
         const int sst = h->st_host->status;
@@ -736,11 +1017,19 @@ int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats)
 {
     if (!h)
         return NSLI_ERR_ARG;
-    MapArgs ma = map_args(h);
-    ma.ignore_done = 1;  // also after a finished run
-    CK(map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
-    CK(reduce_only_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h), h->ybuf),
-       "launch Reduce");
+    if (h->sparse) {
+        SparseArgs sa = h->sp;
+        sa.ignore_done = 1;
+        sa.mode = 1;
+        CK(sparse_row_launch(h->storage == NSLI_F64, h->stream, sa), "launch Map");
+        CK(sparse_col_launch(h->storage == NSLI_F64, h->stream, sa), "launch Reduce");
+    } else {
+        MapArgs ma = map_args(h);
+        ma.ignore_done = 1;  // also after a finished run
+        CK(map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
+        CK(reduce_only_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h), h->ybuf),
+           "launch Reduce");
+    }
     h->launches += 2;
     if (y)
         CK(cudaMemcpyAsync(y, h->ybuf, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy y");
@@ -782,8 +1071,8 @@ int nsli_test_inject_timeout(nsli_handle h, int32_t slot)
 {
     if (!h || slot < 0)
         return NSLI_ERR_ARG;
-    if (h->vpt == 0)
-        return set_err(h, NSLI_ERR_UNSUPPORTED, "long rows are not streamed through bulk copies");
+    if (h->sparse || h->vpt == 0)
+        return set_err(h, NSLI_ERR_UNSUPPORTED, "only the dense register-resident Map streams bulk copies");
     MapArgs ma = map_args(h);
     ma.ignore_done = 1;
     ma.skip_slot = slot;
@@ -804,7 +1093,14 @@ int nsli_get_stored_rows(nsli_handle h, int64_t row0, int64_t rows, double *out)
         return NSLI_OK;
     double *tmp = nullptr;
     CK(cudaMalloc((void **)&tmp, (size_t)rows * h->n * 8), "allocate row copy");
-    cudaError_t e = stored_rows_launch(h->storage, h->stream, h->A, h->scale, h->ld, h->n, row0, rows, tmp);
+    cudaError_t e;
+    if (h->sparse) {
+        e = cudaMemsetAsync(tmp, 0, (size_t)rows * h->n * 8, h->stream);
+        if (e == cudaSuccess)
+            e = sparse_rows_launch(h->storage == NSLI_F64, h->stream, h->sp, row0, rows, tmp);
+    } else {
+        e = stored_rows_launch(h->storage, h->stream, h->A, h->scale, h->ld, h->n, row0, rows, tmp);
+    }
     h->launches += 1;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, tmp, (size_t)rows * h->n * 8, cudaMemcpyDefault, h->stream);

@@ -194,4 +194,41 @@ cudaError_t set_ticks_launch(cudaStream_t s, DevState *const *sts, const long lo
 cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
                                long long n, long long row0, long long rows, double *out);
 
+// ---- sparse A (nsli_sparse.cu) ----------------------------------------------
+// A held as CSR (rows, for the residuals) and CSC (columns, for y), values
+// in the storage type (binary64 or binary32), indices int32, offsets int64.
+struct SparseArgs {
+    const long long *rp;      // m + 1 row offsets
+    const int *ci;            // nnz column indices, ascending within a row
+    const void *va;           // nnz values in row order
+    const long long *cp;      // n + 1 column offsets
+    const int *ri;            // nnz row indices, ascending within a column
+    const void *vc;           // nnz values in column order
+    const void *meta;         // m row records (RowMeta32 / RowMeta64)
+    const int *heavy_rows;    // rows longer than heavy_thr_row, one CTA each
+    const int *heavy_cols;    // columns longer than heavy_thr_col
+    void *coef;               // m: max(r_i, 0) / ||a_i||^2, accumulation type
+    void *x;                  // n, accumulation type
+    double *x64;              // n, the binary64 iterate
+    double *ybuf;             // n: y (ModAP, and the Map-only call)
+    PartStat *part_stat;      // one record per row-pass CTA
+    double *part_dx;          // one partial sum per column / step CTA
+    DevState *st;
+    long long m, n;
+    long long light_rows_per_cta, light_cols_per_cta;
+    long long heavy_thr_row, heavy_thr_col;
+    int n_heavy_rows, n_heavy_cols;
+    int row_light_ctas, col_light_ctas, step_ctas;
+    int w_row, w_col;         // lanes per row / column (1, 2, 4, ..., 32)
+    int ignore_done;          // run even when the done flag is set
+    int mode;                 // 0: iteration; 1: Map and y only (no decision, no step)
+};
+cudaError_t sparse_row_launch(bool f64, cudaStream_t s, const SparseArgs &a);
+cudaError_t sparse_col_launch(bool f64, cudaStream_t s, const SparseArgs &a);
+cudaError_t sparse_step_launch(bool f64, cudaStream_t s, const SparseArgs &a);
+cudaError_t sparse_norms_launch(bool f64, int grid, cudaStream_t s, const SparseArgs &a, double *n2, int *flags);
+cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const SparseArgs &a, const VerifyArgs &v);
+cudaError_t sparse_rows_launch(bool f64, cudaStream_t s, const SparseArgs &a, long long row0, long long rows,
+                               double *out);
+
 }  // namespace nsli

@@ -1,0 +1,542 @@
+// nsli_sparse.cu -- the Map / Reduce / step for a sparse A.
+//
+// Same method as the dense kernels (Section 2 and 3: residuals, positive
+// slices rho+_i of Eq. 7, their sum y, h of Eq. 8, the step of Eq. 8 or
+// Eq. 12, the tick b(k) = b0 + k rho Av of Section 5), for A held twice:
+// compressed rows (CSR) for the residuals and compressed columns (CSC) for
+// y = sum_i c_i a_i, c_i = max(r_i, 0) / ||a_i||^2.  Reading A a second time
+// by columns makes every y_j a sum in one fixed order (rows ascending) with
+// no atomics, so results are bitwise reproducible, at twice the streamed
+// bytes of a single pass.
+//
+// One iteration is three launches (the third only for the ModAP rule):
+//   sparse_row_kernel   r_i, c_i, per-CTA (h, max r, max r/||a||, max |b|);
+//                       the last CTA to finish (ticket) folds the CTA
+//                       records and takes the stop decision.
+//   sparse_col_kernel   y_j in CSC order; the relaxed step x_j -= lambda y_j / h
+//                       in place, or y_j kept for ModAP; per-CTA sums of
+//                       dx^2 (or y^2) folded by the last CTA.
+//   sparse_step_kernel  ModAP only: x_j -= lambda y_j / ||y||.
+// Rows (columns) longer than a threshold are "heavy": one CTA each, at the
+// front of the grid; the other CTAs take fixed ranges of the rest with
+// sub-warp groups of W lanes per row (column).
+#include <cstdint>
+
+#include "nsli.h"
+#include "nsli_internal.h"
+
+namespace nsli {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T> struct SpTraits;
+template <> struct SpTraits<double> {
+    using Meta = RowMeta64;
+};
+template <> struct SpTraits<float> {
+    using Meta = RowMeta32;
+};
+
+template <int W, typename T> __device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T warp_total(T v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Block sum in a fixed tree: warp butterflies, then the 8 warp sums in order.
+template <typename T> __device__ __forceinline__ T block_sum(T v, T *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_total(v);
+    __syncthreads();
+    if (lane == 0)
+        sh[warp] = v;
+    __syncthreads();
+    T t = T(0);
+#pragma unroll
+    for (int q = 0; q < kThreads / 32; ++q)
+        t += sh[q];
+    return t;
+}
+
+struct StatAcc {
+    long long h;
+    double mv, mn, mb;
+};
+
+// Fold per-thread stats into one record (exact: integer sum and maxima).
+__device__ StatAcc block_stats(StatAcc s, StatAcc *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s.h += __shfl_xor_sync(0xffffffffu, s.h, off);
+        s.mv = fmax(s.mv, __shfl_xor_sync(0xffffffffu, s.mv, off));
+        s.mn = fmax(s.mn, __shfl_xor_sync(0xffffffffu, s.mn, off));
+        s.mb = fmax(s.mb, __shfl_xor_sync(0xffffffffu, s.mb, off));
+    }
+    __syncthreads();
+    if (lane == 0)
+        sh[warp] = s;
+    __syncthreads();
+    StatAcc t{0, -INFINITY, -INFINITY, 0.0};
+#pragma unroll
+    for (int q = 0; q < kThreads / 32; ++q) {
+        t.h += sh[q].h;
+        t.mv = fmax(t.mv, sh[q].mv);
+        t.mn = fmax(t.mn, sh[q].mn);
+        t.mb = fmax(t.mb, sh[q].mb);
+    }
+    return t;
+}
+
+// r_i from a finished dot; writes c_i and folds the row into the stats.
+template <typename T>
+__device__ __forceinline__ void finish_row(const SparseArgs &p, long long i, T dot, T tk, StatAcc &s)
+{
+    using Meta = typename SpTraits<T>::Meta;
+    const Meta md = static_cast<const Meta *>(p.meta)[i];
+    const T bi = fma(tk, (T)md.av, (T)md.b0);
+    const T ri = dot - bi;
+    const bool viol = ri > T(0);
+    static_cast<T *>(p.coef)[i] = viol ? ri * (T)md.inv_n2 : T(0);
+    s.h += viol ? 1 : 0;
+    s.mv = fmax(s.mv, (double)ri);
+    s.mn = fmax(s.mn, (double)(ri * (T)md.inv_n));
+    const T ab = bi < T(0) ? -bi : bi;
+    s.mb = fmax(s.mb, (double)ab);
+}
+
+// Stop decision of the iteration whose Map just finished (same rules and
+// order as the dense reduce kernel): candidate stop, iteration cap, or step.
+__device__ void decide(DevState *st, const StatAcc &t, int mode)
+{
+    st->h = t.h;
+    st->maxviol = t.mv;
+    st->maxnorm = t.mn;
+    st->maxb = t.mb;
+    if (mode != 0)
+        return;
+    const int stop = st->stop;
+    const double eps = st->eps;
+    const bool force = st->force_step != 0;
+    const bool pass = !force && ((stop != NSLI_STOP_NONE && t.h == 0) || (stop == NSLI_STOP_EPSMEM && t.mn < eps) ||
+                                 (stop == NSLI_STOP_MAXVIOL_REL && t.mv <= eps * t.mb));
+    const bool at_max = !pass && (st->it >= st->max_iter);
+    if (pass) {
+        st->status = ST_CANDIDATE;
+        st->done = 1;
+    } else if (at_max) {
+        st->status = NSLI_NOT_CONVERGED;
+        st->done = 1;
+    }
+    st->force_step = 0;
+}
+
+// Bookkeeping after a step (the dense reduce kernel's, in the same order).
+__device__ void finish_step(DevState *st, double dx2, double ynorm)
+{
+    st->it += 1;
+    if (!st->hold_tick)
+        st->tick += 1;
+    st->dx_norm = sqrt(dx2);
+    st->y_norm = ynorm;
+    if (st->stop == NSLI_STOP_STEP && sqrt(dx2) < st->eps) {
+        st->status = NSLI_OK;
+        st->done = 1;
+    }
+}
+
+// Ticket: true in exactly one thread block, the last to arrive.
+__device__ __forceinline__ bool last_block(DevState *st, int nblk, int *sh_last)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(&st->ticket, 1u);
+        *sh_last = (t == (unsigned int)nblk - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*sh_last)
+        return false;
+    __threadfence();
+    return true;
+}
+
+template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_row_kernel(const SparseArgs p)
+{
+    DevState *st = p.st;
+    if (!p.ignore_done && *(volatile int *)&st->done)
+        return;
+    __shared__ StatAcc sh_stat[kThreads / 32];
+    __shared__ T sh_sum[kThreads / 32];
+    __shared__ int sh_last;
+    const T *va = static_cast<const T *>(p.va);
+    const T *x = static_cast<const T *>(p.x);
+    const T tk = (T)((double)st->tick * st->rho);
+    StatAcc s{0, -INFINITY, -INFINITY, 0.0};
+    const int nblk = p.n_heavy_rows + p.row_light_ctas;
+
+    if ((int)blockIdx.x < p.n_heavy_rows) {
+        // a heavy row: the whole block, then a fixed-order block sum
+        const long long i = p.heavy_rows[blockIdx.x];
+        const long long e0 = p.rp[i], e1 = p.rp[i + 1];
+        T acc = T(0);
+        for (long long e = e0 + threadIdx.x; e < e1; e += kThreads)
+            acc = fma(va[e], __ldg(x + p.ci[e]), acc);
+        const T dot = block_sum(acc, sh_sum);
+        if (threadIdx.x == 0)
+            finish_row(p, i, dot, tk, s);
+    } else {
+        const long long b = blockIdx.x - p.n_heavy_rows;
+        const long long r0 = b * p.light_rows_per_cta;
+        const long long r1 = min(r0 + p.light_rows_per_cta, p.m);
+        constexpr int groups = kThreads / W;
+        const int g = threadIdx.x / W, l = threadIdx.x % W;
+        // every group makes the same number of passes, so the shuffles
+        // below always see all 32 lanes of a warp
+        for (long long base = r0; base < r1; base += groups) {
+            const long long i = base + g;
+            T acc = T(0);
+            bool valid = i < r1;
+            long long e0 = 0, e1 = 0;
+            if (valid) {
+                e0 = p.rp[i];
+                e1 = p.rp[i + 1];
+                valid = (e1 - e0) <= p.heavy_thr_row;
+            }
+            if (valid)
+                for (long long e = e0 + l; e < e1; e += W)
+                    acc = fma(va[e], __ldg(x + p.ci[e]), acc);
+            const T dot = group_sum<W>(acc);
+            if (valid && l == 0)
+                finish_row(p, i, dot, tk, s);
+        }
+    }
+    const StatAcc t = block_stats(s, sh_stat);
+    if (threadIdx.x == 0) {
+        PartStat ps;
+        ps.h = t.h;
+        ps.maxviol = t.mv;
+        ps.maxnorm = t.mn;
+        ps.maxb = t.mb;
+        p.part_stat[blockIdx.x] = ps;
+    }
+    if (!last_block(st, nblk, &sh_last))
+        return;
+    StatAcc u{0, -INFINITY, -INFINITY, 0.0};
+    for (int q = threadIdx.x; q < nblk; q += kThreads) {
+        const PartStat *ps = p.part_stat + q;
+        u.h += __ldcg(&ps->h);
+        u.mv = fmax(u.mv, __ldcg(&ps->maxviol));
+        u.mn = fmax(u.mn, __ldcg(&ps->maxnorm));
+        u.mb = fmax(u.mb, __ldcg(&ps->maxb));
+    }
+    const StatAcc tot = block_stats(u, sh_stat);
+    if (threadIdx.x == 0) {
+        decide(st, tot, p.mode);
+        st->ticket = 0u;
+    }
+}
+
+// y_j = sum over the column's entries (rows ascending) of c_i a_ij.
+template <typename T>
+__device__ __forceinline__ double col_update(const SparseArgs &p, long long j, T y, double s_relaxed, int rule)
+{
+    if (p.mode != 0) {
+        p.ybuf[j] = (double)y;
+        return 0.0;
+    }
+    if (rule == NSLI_RULE_MODAP) {
+        const double yd = (double)y;
+        p.ybuf[j] = yd;
+        return yd * yd;
+    }
+    const double xo = p.x64[j];
+    const double xn = xo - s_relaxed * (double)y;
+    p.x64[j] = xn;
+    static_cast<T *>(p.x)[j] = (T)xn;
+    const double d = xn - xo;
+    return d * d;
+}
+
+template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_col_kernel(const SparseArgs p)
+{
+    DevState *st = p.st;
+    if (!p.ignore_done && *(volatile int *)&st->done)
+        return;
+    __shared__ T sh_sum[kThreads / 32];
+    __shared__ double sh_d[kThreads / 32];
+    __shared__ int sh_last;
+    const T *vc = static_cast<const T *>(p.vc);
+    const T *coef = static_cast<const T *>(p.coef);
+    const long long h = st->h;
+    const int rule = st->rule;
+    const double s_relaxed = h > 0 ? st->lambda / (double)h : 0.0;
+    const int nblk = p.n_heavy_cols + p.col_light_ctas;
+    double part = 0.0;
+
+    if ((int)blockIdx.x < p.n_heavy_cols) {
+        const long long j = p.heavy_cols[blockIdx.x];
+        const long long e0 = p.cp[j], e1 = p.cp[j + 1];
+        T acc = T(0);
+        for (long long e = e0 + threadIdx.x; e < e1; e += kThreads)
+            acc = fma(__ldg(coef + p.ri[e]), vc[e], acc);
+        const T y = block_sum(acc, sh_sum);
+        if (threadIdx.x == 0)
+            part = col_update(p, j, y, s_relaxed, rule);
+    } else {
+        const long long b = blockIdx.x - p.n_heavy_cols;
+        const long long c0 = b * p.light_cols_per_cta;
+        const long long c1 = min(c0 + p.light_cols_per_cta, p.n);
+        constexpr int groups = kThreads / W;
+        const int g = threadIdx.x / W, l = threadIdx.x % W;
+        for (long long base = c0; base < c1; base += groups) {
+            const long long j = base + g;
+            T acc = T(0);
+            bool valid = j < c1;
+            long long e0 = 0, e1 = 0;
+            if (valid) {
+                e0 = p.cp[j];
+                e1 = p.cp[j + 1];
+                valid = (e1 - e0) <= p.heavy_thr_col;
+            }
+            if (valid)
+                for (long long e = e0 + l; e < e1; e += W)
+                    acc = fma(__ldg(coef + p.ri[e]), vc[e], acc);
+            const T y = group_sum<W>(acc);
+            if (valid && l == 0)
+                part += col_update(p, j, y, s_relaxed, rule);
+        }
+    }
+    const double bsum = block_sum(part, sh_d);
+    if (threadIdx.x == 0)
+        p.part_dx[blockIdx.x] = bsum;
+    if (!last_block(st, nblk, &sh_last))
+        return;
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += kThreads)
+        v += __ldcg(p.part_dx + q);
+    const double tot = block_sum(v, sh_d);
+    if (threadIdx.x == 0) {
+        if (p.mode == 0) {
+            if (rule == NSLI_RULE_MODAP)
+                st->y_norm = sqrt(tot);
+            else
+                finish_step(st, tot, 0.0);
+        }
+        st->ticket = 0u;
+    }
+}
+
+template <typename T> __global__ void __launch_bounds__(kThreads) sparse_step_kernel(const SparseArgs p)
+{
+    DevState *st = p.st;
+    if (*(volatile int *)&st->done || st->rule != NSLI_RULE_MODAP)
+        return;
+    __shared__ double sh_d[kThreads / 32];
+    __shared__ int sh_last;
+    const double ynorm = st->y_norm;
+    const double s = ynorm > 0.0 ? st->lambda / ynorm : 0.0;
+    T *x = static_cast<T *>(p.x);
+    double v = 0.0;
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < p.n; j += (long long)gridDim.x * kThreads) {
+        const double xo = p.x64[j];
+        const double xn = xo - s * __ldcg(p.ybuf + j);
+        p.x64[j] = xn;
+        x[j] = (T)xn;
+        const double d = xn - xo;
+        v += d * d;
+    }
+    const double bsum = block_sum(v, sh_d);
+    if (threadIdx.x == 0)
+        p.part_dx[blockIdx.x] = bsum;
+    if (!last_block(st, gridDim.x, &sh_last))
+        return;
+    double w = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += kThreads)
+        w += __ldcg(p.part_dx + q);
+    const double tot = block_sum(w, sh_d);
+    if (threadIdx.x == 0) {
+        finish_step(st, tot, ynorm);
+        st->ticket = 0u;
+    }
+}
+
+// ---- set-up and the binary64 check -----------------------------------------
+
+__device__ __forceinline__ unsigned long long sp_ord_enc(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// One warp per row: binary64 ||a_i||^2 of the stored values (fixed tree),
+// zero-row and finiteness flags.
+template <typename T> __global__ void __launch_bounds__(kThreads) sparse_norms_kernel(const SparseArgs p, double *n2,
+                                                                                   int *flags)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kThreads) >> 5;
+    const T *va = static_cast<const T *>(p.va);
+    for (long long i = w; i < p.m; i += nw) {
+        double s = 0.0;
+        int bad = 0;
+        for (long long e = p.rp[i] + lane; e < p.rp[i + 1]; e += 32) {
+            const double a = (double)va[e];
+            if (!isfinite(a))
+                bad = 1;
+            s = fma(a, a, s);
+        }
+        s = warp_total(s);
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            n2[i] = s;
+            if (bad)
+                atomicOr(flags, PREPF_NONFINITE);
+            else if (s == 0.0)
+                atomicOr(flags, PREPF_ZERO_ROW);
+        }
+    }
+}
+
+// One warp per row: r_i in binary64 from the stored values and x64; maxima
+// by order-preserving integer atomics (exact, schedule-independent).
+template <typename T> __global__ void __launch_bounds__(kThreads) sparse_verify_kernel(const SparseArgs p,
+                                                                                    const VerifyArgs v)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kThreads) >> 5;
+    const T *va = static_cast<const T *>(p.va);
+    const double kr = __dmul_rn((double)v.st->tick, v.st->rho);
+    double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+    unsigned long long h = 0;
+    for (long long i = w; i < p.m; i += nw) {
+        double s = 0.0;
+        for (long long e = p.rp[i] + lane; e < p.rp[i + 1]; e += 32)
+            s = fma((double)va[e], v.x64[p.ci[e]], s);
+        s = warp_total(s);
+        const double bi = __dadd_rn(v.b0_64[i], __dmul_rn(kr, v.av_64[i]));
+        const double ri = s - bi;
+        mv = fmax(mv, ri);
+        mn = fmax(mn, ri / sqrt(v.n2_64[i]));
+        mb = fmax(mb, fabs(bi));
+        h += (ri > 0.0) ? 1ull : 0ull;
+    }
+    if (lane == 0) {
+        atomicMax(&v.out->maxviol, sp_ord_enc(mv));
+        atomicMax(&v.out->maxnorm, sp_ord_enc(mn));
+        atomicMax(&v.out->maxb, sp_ord_enc(mb));
+        atomicAdd(&v.out->h, h);
+    }
+}
+
+// Dense copies of stored rows row0 .. row0+rows-1 (out zeroed by the caller).
+template <typename T> __global__ void sparse_rows_kernel(const SparseArgs p, long long row0, long long rows,
+                                                         double *out)
+{
+    const long long r = blockIdx.x;
+    if (r >= rows)
+        return;
+    const long long i = row0 + r;
+    const T *va = static_cast<const T *>(p.va);
+    for (long long e = p.rp[i] + threadIdx.x; e < p.rp[i + 1]; e += blockDim.x)
+        out[r * p.n + p.ci[e]] = (double)va[e];
+}
+
+template <typename T> cudaError_t row_launch(int w, unsigned grid, cudaStream_t s, const SparseArgs &a)
+{
+    switch (w) {
+    case 1: sparse_row_kernel<T, 1><<<grid, kThreads, 0, s>>>(a); break;
+    case 2: sparse_row_kernel<T, 2><<<grid, kThreads, 0, s>>>(a); break;
+    case 4: sparse_row_kernel<T, 4><<<grid, kThreads, 0, s>>>(a); break;
+    case 8: sparse_row_kernel<T, 8><<<grid, kThreads, 0, s>>>(a); break;
+    case 16: sparse_row_kernel<T, 16><<<grid, kThreads, 0, s>>>(a); break;
+    case 32: sparse_row_kernel<T, 32><<<grid, kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t col_launch(int w, unsigned grid, cudaStream_t s, const SparseArgs &a)
+{
+    switch (w) {
+    case 1: sparse_col_kernel<T, 1><<<grid, kThreads, 0, s>>>(a); break;
+    case 2: sparse_col_kernel<T, 2><<<grid, kThreads, 0, s>>>(a); break;
+    case 4: sparse_col_kernel<T, 4><<<grid, kThreads, 0, s>>>(a); break;
+    case 8: sparse_col_kernel<T, 8><<<grid, kThreads, 0, s>>>(a); break;
+    case 16: sparse_col_kernel<T, 16><<<grid, kThreads, 0, s>>>(a); break;
+    case 32: sparse_col_kernel<T, 32><<<grid, kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sparse_row_launch(bool f64, cudaStream_t s, const SparseArgs &a)
+{
+    const unsigned grid = (unsigned)(a.n_heavy_rows + a.row_light_ctas);
+    return f64 ? row_launch<double>(a.w_row, grid, s, a) : row_launch<float>(a.w_row, grid, s, a);
+}
+
+cudaError_t sparse_col_launch(bool f64, cudaStream_t s, const SparseArgs &a)
+{
+    const unsigned grid = (unsigned)(a.n_heavy_cols + a.col_light_ctas);
+    return f64 ? col_launch<double>(a.w_col, grid, s, a) : col_launch<float>(a.w_col, grid, s, a);
+}
+
+cudaError_t sparse_step_launch(bool f64, cudaStream_t s, const SparseArgs &a)
+{
+    const unsigned grid = (unsigned)a.step_ctas;
+    if (f64)
+        sparse_step_kernel<double><<<grid, kThreads, 0, s>>>(a);
+    else
+        sparse_step_kernel<float><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sparse_norms_launch(bool f64, int grid, cudaStream_t s, const SparseArgs &a, double *n2, int *flags)
+{
+    if (f64)
+        sparse_norms_kernel<double><<<grid, kThreads, 0, s>>>(a, n2, flags);
+    else
+        sparse_norms_kernel<float><<<grid, kThreads, 0, s>>>(a, n2, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const SparseArgs &a, const VerifyArgs &v)
+{
+    if (f64)
+        sparse_verify_kernel<double><<<grid, kThreads, 0, s>>>(a, v);
+    else
+        sparse_verify_kernel<float><<<grid, kThreads, 0, s>>>(a, v);
+    return cudaGetLastError();
+}
+
+cudaError_t sparse_rows_launch(bool f64, cudaStream_t s, const SparseArgs &a, long long row0, long long rows,
+                               double *out)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (f64)
+        sparse_rows_kernel<double><<<(unsigned)rows, 128, 0, s>>>(a, row0, rows, out);
+    else
+        sparse_rows_kernel<float><<<(unsigned)rows, 128, 0, s>>>(a, row0, rows, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nsli

@@ -61,7 +61,7 @@ class NsliError(RuntimeError):
 
 _lib = None
 _lock = threading.Lock()
-EXPORTS = ["nsli_create", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
+EXPORTS = ["nsli_create", "nsli_create_csr", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
            "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
            "nsli_get_stored_rows", "nsli_get_norms2", "nsli_test_inject_timeout",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
@@ -95,6 +95,8 @@ def load(path: str | None = None):
         H = ctypes.c_void_p
         lib.nsli_create.argtypes = [ctypes.POINTER(H), i64, i64, i32, i32, P, i64, P, P, P, P, P]
         lib.nsli_create.restype = ctypes.c_int
+        lib.nsli_create_csr.argtypes = [ctypes.POINTER(H), i64, i64, i32, i64, P, P, P, P, P, P, P, P]
+        lib.nsli_create_csr.restype = ctypes.c_int
         lib.nsli_update_b.argtypes = [H, P, i64]
         lib.nsli_update_b.restype = ctypes.c_int
         lib.nsli_iterate.argtypes = [H, ctypes.POINTER(nsli_params), i64]
@@ -390,6 +392,35 @@ class Solver:
 
     def sync(self):
         _check(load().nsli_sync(self._h), "nsli_sync", self._h)
+
+
+class SparseSolver(Solver):
+    """One problem with a sparse A in compressed-row form (row_ptr int64,
+    col_idx int32 strictly increasing within a row, val float64), resident
+    on the current CUDA device.  ``storage`` is "f64" or "f32".  Every
+    Solver method applies (inject_timeout reports ERR_UNSUPPORTED)."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val, b0, x0, Av=None, norms2=None, storage="f32",
+                 stream=None):
+        lib = load()
+        m, n = int(m), int(n)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        if row_ptr.shape != (m + 1,) or col_idx.shape != val.shape or col_idx.ndim != 1:
+            raise ValueError("row_ptr must have m + 1 entries and col_idx / val nnz entries")
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        b0, x0, Av, norms2 = _f64(b0, m), _f64(x0, n), _f64(Av, m), _f64(norms2, m)
+        _sync_torch_inputs(b0, x0, Av, norms2)
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream)
+        rc = lib.nsli_create_csr(ctypes.byref(h), m, n, self.storage, int(col_idx.size), _ptr(row_ptr),
+                                 _ptr(col_idx), _ptr(val), _ptr(b0), _ptr(norms2), _ptr(Av), _ptr(x0), s)
+        if rc != OK:
+            raise NsliError(rc, "nsli_create_csr")
+        self._h = h
+        self.m, self.n = m, n
+        self.nnz = int(col_idx.size)
 
 
 class BatchSolver:

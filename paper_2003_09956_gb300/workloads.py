@@ -189,7 +189,7 @@ def _csr_rows_dot(rp: np.ndarray, ci: np.ndarray, val: np.ndarray, v: np.ndarray
 
 
 def sparse_system(m: int, n: int, k: int, seed: int, x0_std: float = 5.0,
-                  lengths: np.ndarray | None = None) -> dict:
+                  lengths: np.ndarray | None = None, dense_cols: int = 0) -> dict:
     """Sparse non-stationary random system in compressed-row form.
 
     Row i has k non-zeros (or ``lengths[i]``) at distinct columns, ascending;
@@ -198,7 +198,8 @@ def sparse_system(m: int, n: int, k: int, seed: int, x0_std: float = 5.0,
     x0 ~ N(0, x0_std^2 I) rounded to binary32.  With a fixed k the columns of
     a row are a sorted sample with replacement from [0, n - k] plus 0..k-1
     (distinct by construction); with ``lengths`` each row is a uniform
-    sample without replacement."""
+    sample without replacement, and ``dense_cols`` > 0 puts columns
+    0 .. dense_cols-1 into every row (counted in its length)."""
     g = np.random.Generator(np.random.PCG64(seed))
     if lengths is None:
         if not 1 <= k <= n:
@@ -216,13 +217,15 @@ def sparse_system(m: int, n: int, k: int, seed: int, x0_std: float = 5.0,
             val[r0 * k:r1 * k] = g.standard_normal((r1 - r0) * k, dtype=np.float32)
     else:
         lengths = np.asarray(lengths, dtype=np.int64)
-        if lengths.shape != (m,) or lengths.min() < 1 or lengths.max() > n:
-            raise ValueError("lengths must hold m values in [1, n]")
+        if lengths.shape != (m,) or lengths.min() < max(1, dense_cols) or lengths.max() > n:
+            raise ValueError("lengths must hold m values in [max(1, dense_cols), n]")
         rp = np.zeros(m + 1, np.int64)
         np.cumsum(lengths, out=rp[1:])
         ci = np.empty(int(rp[-1]), np.int32)
+        head = np.arange(dense_cols)
         for i in range(m):
-            ci[rp[i]:rp[i + 1]] = np.sort(g.choice(n, int(lengths[i]), replace=False))
+            rest = g.choice(n - dense_cols, int(lengths[i]) - dense_cols, replace=False) + dense_cols
+            ci[rp[i]:rp[i + 1]] = np.concatenate([head, np.sort(rest)])
         val = g.standard_normal(ci.size, dtype=np.float32).astype(np.float64)
     z = g.uniform(-1.0, 1.0, n)
     slack = g.uniform(0.1, 1.0, m)

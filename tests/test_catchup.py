@@ -85,3 +85,12 @@ def test_oracle_modap_outruns_relaxed_on_model_system():
     lo_r, _, _ = catchup.max_rate(oracle_trial(p, oracle.RULE_RELAXED, 1.0, eps, K), 1e-9, steps=8)
     assert 0 < lo_m * math.sqrt(n) <= lam
     assert lo_r < 1e-3 * lo_m
+
+
+def test_sparse_model_system_translation_matches_dense():
+    from paper_2003_09956_gb300 import workloads
+    p = catchup.model_system_translated_csr(6, seed=1)
+    q = catchup.model_system_translated(6, seed=1)
+    np.testing.assert_array_equal(workloads.csr_to_dense(p["rp"], p["ci"], p["val"], 6), q["A"])
+    np.testing.assert_array_equal(p["Av"], q["Av"])
+    np.testing.assert_array_equal(p["x0"], q["x0"])
