@@ -47,6 +47,12 @@ BATCHED = {
     # a quarter of the rows, for profiler captures (A = 256 MiB bf16 > L2)
     "batched-16384x8192x64": {"m": 16384, "n": 8192, "P": 64, "rho": 1e-4, "seed": 2009},
 }
+SPARSE = {
+    # k = 32 random columns per row (compressed rows + compressed columns,
+    # 2 x 1.07 GB of binary32 entries and indices: larger than L2)
+    "sparse-4194304x1048576x32": {"m": 1 << 22, "n": 1 << 20, "k": 32, "rho": 1e-4, "seed": 2011},
+    "sparse-1048576x262144x32": {"m": 1 << 20, "n": 1 << 18, "k": 32, "rho": 1e-4, "seed": 2012},
+}
 METRIC = "ModAP iterations/sec"
 UNIT = "iterations/s"
 
@@ -65,6 +71,9 @@ def parse_args():
                     help="batched tensor-core workload measured in the same run ('' for none)")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the batched workload (profiling entry)")
+    ap.add_argument("--sparse", default="sparse-4194304x1048576x32",
+                    help="sparse workload measured in the same run ('' for none)")
+    ap.add_argument("--sparse-only", action="store_true", help="time only the sparse workload")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the serving stream measured in the same run (0: none)")
     ap.add_argument("--serving-only", action="store_true", help="time only the serving stream")
@@ -78,6 +87,20 @@ def map_bytes(m, n, storage):
     FP8 row scale) per-row record b0, Av, 1/||a||^2, and x."""
     per_row = 16 if storage == "fp8" else 12
     return m * n * ELEM_BYTES[storage] + m * per_row + 4 * n
+
+
+def sparse_bytes(m, n, nnz, storage):
+    """Algorithmic bytes of one sparse iteration, per kernel: the row pass
+    reads the row offsets, column indices and entries, the 16-byte row record
+    (b0, Av, 1/||a||^2, 1/||a||; 32 in binary64), x once, and writes the
+    slice coefficients; the column pass reads the column offsets, row indices
+    and entries, the coefficients once, and reads/writes x (binary64 and its
+    rounding)."""
+    eb = ELEM_BYTES[storage]
+    rec = 32 if storage == "f64" else 16
+    row = 8 * (m + 1) + nnz * (4 + eb) + rec * m + eb * n + eb * m
+    col = 8 * (n + 1) + nnz * (4 + eb) + eb * m + n * (8 + 8 + eb)
+    return row, col
 
 
 def step_bytes(m, n, storage):
@@ -249,6 +272,46 @@ def time_batched(nsli, torch, name, steps, warmup):
             "max_viol_f64_first_problems": [float(v) for v in mv[:4]]}
 
 
+def time_sparse(nsli, torch, name, steps, warmup, peak):
+    """Iterations of the sparse system (relaxed rule, binary32 entries)."""
+    from paper_2003_09956_gb300 import workloads
+
+    w = SPARSE[name]
+    t0 = time.perf_counter()
+    p = workloads.sparse_system(w["m"], w["n"], w["k"], seed=w["seed"])
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    s = nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"], Av=p["Av"],
+                          storage="f32", stream=stream.cuda_stream)
+    B = min(steps, 50)
+    s.iterate(max(warmup, B), rho=w["rho"], block_iters=B)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        s.iterate(steps, rho=w["rho"], block_iters=B)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = s.launch_count() - l0
+    kpass = min(steps, 100)
+    row_ms, col_ms = s.iterate_timed(kpass, rho=w["rho"])
+    mv, _ = s.residual_max()
+    s.close()
+    rb, cb = sparse_bytes(p["m"], p["n"], p["nnz"], "f32")
+    row_gbs = rb / (row_ms / kpass / 1e3) / 1e9
+    col_gbs = cb / (col_ms / kpass / 1e3) / 1e9
+    return {"workload": name + " f32, rho=%g per tick, RELAXED lambda=1" % w["rho"], "nnz": p["nnz"],
+            "value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms,
+            "row_kernel_ms": row_ms / kpass, "col_kernel_ms": col_ms / kpass,
+            "row_kernel_gbs": row_gbs, "col_kernel_gbs": col_gbs,
+            "row_frac_of_measured_hbm": row_gbs / peak, "col_frac_of_measured_hbm": col_gbs / peak,
+            "algorithmic_bytes_per_step": rb + cb, "gpu_launches": launches,
+            "max_viol_f64": mv, "generate_s": t_gen}
+
+
 SERVE = {"rate": 200.0, "tick_s": 0.010, "rho": 1e-4, "eps": 1e-6, "max_iter": 300, "seed": 2010,
          "classes": [int(round(512 * 2 ** (k / 2))) for k in range(11)], "c": [2, 4, 8]}
 
@@ -415,6 +478,12 @@ def main():
             print(json.dumps({"metric": "serving solves/sec", "value": r["solves_per_s"], "unit": "solves/s",
                               "config": {"workload": "poisson-200/s mixed-size bf16 stream"}, **r}), flush=True)
         return 0
+    if args.sparse_only:
+        peak, _ = measured_peak()
+        r = time_sparse(nsli, torch, args.sparse, args.steps, max(3, args.warmup), peak)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "config": {"workload": args.sparse}, **r}), flush=True)
+        return 0
     if args.batched_only:
         r = time_batched(nsli, torch, args.batched, args.steps, max(3, args.warmup))
         if rank == 0:
@@ -476,6 +545,8 @@ def main():
                         "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
 
     variants["model_system_f64"] = time_model_system(nsli)
+    if args.sparse:
+        variants["sparse_f32"] = time_sparse(nsli, torch, args.sparse, K, W, peak)
     if args.batched:
         variants["batched_bf16"] = time_batched(nsli, torch, args.batched, min(K, 100), W)
     if args.serve_seconds > 0 and world == 1:

@@ -48,8 +48,9 @@ struct nsli_solver {
     bool sparse = false;
     long long nnz = 0;
     long long *rp = nullptr, *cp = nullptr;
-    int *ci = nullptr, *ri = nullptr, *heavy_rows = nullptr, *heavy_cols = nullptr;
-    void *va = nullptr, *vc = nullptr, *coef = nullptr;
+    int *ci = nullptr, *ri = nullptr, *row_cnt = nullptr, *col_cnt = nullptr;
+    SegPiece *row_pieces = nullptr, *col_pieces = nullptr;
+    void *va = nullptr, *vc = nullptr, *coef = nullptr, *row_slots = nullptr, *col_slots = nullptr;
     SparseArgs sp{};
 
     cudaGraphExec_t graph = nullptr;
@@ -106,7 +107,8 @@ void free_all(nsli_solver *h)
     void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
                    h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags,
                    (h->x64 != h->x) ? (void *)h->x64 : nullptr,
-                   h->rp, h->cp, h->ci, h->ri, h->heavy_rows, h->heavy_cols, h->va, h->vc, h->coef};
+                   h->rp, h->cp, h->ci, h->ri, h->row_cnt, h->col_cnt, h->row_pieces, h->col_pieces,
+                   h->va, h->vc, h->coef, h->row_slots, h->col_slots};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -643,8 +645,9 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
         }
 
     // lanes per row / column from the median length (a few very long rows or
-    // columns do not set it); those longer than 256 passes of that width get
-    // a CTA each
+    // columns do not set it): W lanes x 4 loads cover a typical one in one
+    // chunk; those needing more than 4 chunks are cut into pieces of
+    // kSparsePiece entries, one CTA each
     auto median_len = [](const std::vector<long long> &off) {
         std::vector<long long> len(off.size() - 1);
         for (size_t i = 0; i + 1 < off.size(); ++i)
@@ -654,9 +657,35 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     };
     auto pick_w = [](double typical) {
         int w = 1;
-        while (w < 32 && w < typical / 2.0)
+        while (w < 32 && 4.0 * w < typical)
             w *= 2;
         return w;
+    };
+    auto make_pieces = [](const std::vector<long long> &off, long long thr, std::vector<SegPiece> &pcs,
+                          long long *nseg, long long *nslots) {
+        long long hs = 0, slot = 0;
+        for (size_t q = 0; q + 1 < off.size(); ++q) {
+            const long long len = off[q + 1] - off[q];
+            if (len <= thr)
+                continue;
+            const int np = (int)((len + kSparsePiece - 1) / kSparsePiece);
+            for (int k = 0; k < np; ++k) {
+                SegPiece pc;
+                pc.seg = (int)q;
+                pc.hs = (int)hs;
+                pc.first = (int)slot;
+                pc.npieces = np;
+                pc.k = k;
+                pc.pad = 0;
+                pc.e0 = off[q] + (long long)k * kSparsePiece;
+                pc.e1 = std::min(off[q + 1], pc.e0 + kSparsePiece);
+                pcs.push_back(pc);
+            }
+            slot += np;
+            hs += 1;
+        }
+        *nseg = hs;
+        *nslots = slot;
     };
     SparseArgs &sp = h->sp;
     sp = SparseArgs{};
@@ -664,29 +693,31 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     sp.n = n;
     sp.w_row = pick_w(median_len(rp));
     sp.w_col = pick_w(median_len(cp));
-    sp.heavy_thr_row = std::max<long long>(512, 256ll * sp.w_row);
-    sp.heavy_thr_col = std::max<long long>(512, 256ll * sp.w_col);
-    std::vector<int> hr, hc;
-    for (long long i = 0; i < m; ++i)
-        if (rp[i + 1] - rp[i] > sp.heavy_thr_row)
-            hr.push_back((int)i);
-    for (long long j = 0; j < n; ++j)
-        if (cp[j + 1] - cp[j] > sp.heavy_thr_col)
-            hc.push_back((int)j);
-    sp.n_heavy_rows = (int)hr.size();
-    sp.n_heavy_cols = (int)hc.size();
-    auto split = [&](long long items, int w, int *ctas, long long *per) {
+    sp.heavy_thr_row = 16ll * sp.w_row;
+    sp.heavy_thr_col = 16ll * sp.w_col;
+    std::vector<SegPiece> hr, hc;
+    long long nseg_r = 0, nslot_r = 0, nseg_c = 0, nslot_c = 0;
+    make_pieces(rp, sp.heavy_thr_row, hr, &nseg_r, &nslot_r);
+    make_pieces(cp, sp.heavy_thr_col, hc, &nseg_c, &nslot_c);
+    if (hr.size() > (size_t)INT_MAX / 2 || hc.size() > (size_t)INT_MAX / 2)
+        return fail(set_err(h, NSLI_ERR_UNSUPPORTED, "too many heavy pieces"));
+    sp.n_row_pieces = (int)hr.size();
+    sp.n_col_pieces = (int)hc.size();
+    int row_bps = 0, col_bps = 0;
+    sparse_blocks_per_sm(storage == NSLI_F64, sp.w_row, sp.w_col, &row_bps, &col_bps);
+    auto split = [&](long long items, int w, int bps, int *ctas, long long *per) {
         const long long groups = 256 / w;
-        long long c = (items + groups * 4 - 1) / (groups * 4);
-        c = std::max<long long>(1, std::min<long long>(c, (long long)h->num_sms * 8));
+        const long long cap = (long long)h->num_sms * std::max(1, bps);
+        long long c = (items + groups - 1) / groups;
+        c = std::max<long long>(1, std::min<long long>(c, cap));
         *per = (items + c - 1) / c;
         *ctas = (int)((items + *per - 1) / *per);
     };
-    split(m, sp.w_row, &sp.row_light_ctas, &sp.light_rows_per_cta);
-    split(n, sp.w_col, &sp.col_light_ctas, &sp.light_cols_per_cta);
+    split(m, sp.w_row, row_bps, &sp.row_light_ctas, &sp.light_rows_per_cta);
+    split(n, sp.w_col, col_bps, &sp.col_light_ctas, &sp.light_cols_per_cta);
     sp.step_ctas = (int)std::max<long long>(1, std::min<long long>((n + 1023) / 1024, (long long)h->num_sms * 4));
-    const long long g_row = sp.n_heavy_rows + sp.row_light_ctas;
-    const long long g_col = std::max<long long>(sp.n_heavy_cols + sp.col_light_ctas, sp.step_ctas);
+    const long long g_row = sp.n_row_pieces + sp.row_light_ctas;
+    const long long g_col = std::max<long long>(sp.n_col_pieces + sp.col_light_ctas, sp.step_ctas);
     h->G = (int)g_row;
 
     if (stream) {
@@ -703,10 +734,16 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     CKC(cudaMalloc((void **)&h->cp, (size_t)(n + 1) * 8), "allocate column offsets");
     CKC(cudaMalloc((void **)&h->ri, (size_t)nnz * 4), "allocate row indices");
     CKC(cudaMalloc(&h->vc, (size_t)nnz * eb), "allocate column values");
-    if (!hr.empty())
-        CKC(cudaMalloc((void **)&h->heavy_rows, hr.size() * 4), "allocate heavy rows");
-    if (!hc.empty())
-        CKC(cudaMalloc((void **)&h->heavy_cols, hc.size() * 4), "allocate heavy columns");
+    if (!hr.empty()) {
+        CKC(cudaMalloc((void **)&h->row_pieces, hr.size() * sizeof(SegPiece)), "allocate heavy row pieces");
+        CKC(cudaMalloc(&h->row_slots, (size_t)nslot_r * eb), "allocate heavy row slots");
+        CKC(cudaMalloc((void **)&h->row_cnt, (size_t)nseg_r * 4), "allocate heavy row counters");
+    }
+    if (!hc.empty()) {
+        CKC(cudaMalloc((void **)&h->col_pieces, hc.size() * sizeof(SegPiece)), "allocate heavy column pieces");
+        CKC(cudaMalloc(&h->col_slots, (size_t)nslot_c * eb), "allocate heavy column slots");
+        CKC(cudaMalloc((void **)&h->col_cnt, (size_t)nseg_c * 4), "allocate heavy column counters");
+    }
     CKC(cudaMalloc(&h->coef, (size_t)m * eb), "allocate slice coefficients");
     CKC(cudaMalloc(&h->meta, (size_t)m * 32), "allocate row records");
     CKC(cudaMalloc((void **)&h->b0_64, (size_t)m * 8), "allocate b0");
@@ -743,11 +780,16 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     CKC(cudaMemcpyAsync(h->cp, cp.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s), "upload column offsets");
     CKC(cudaMemcpyAsync(h->ri, ri.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s), "upload row indices");
     CKC(cudaMemcpyAsync(h->vc, vc_src, (size_t)nnz * eb, cudaMemcpyHostToDevice, s), "upload column values");
-    if (!hr.empty())
-        CKC(cudaMemcpyAsync(h->heavy_rows, hr.data(), hr.size() * 4, cudaMemcpyHostToDevice, s), "upload heavy rows");
-    if (!hc.empty())
-        CKC(cudaMemcpyAsync(h->heavy_cols, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, s),
-            "upload heavy columns");
+    if (!hr.empty()) {
+        CKC(cudaMemcpyAsync(h->row_pieces, hr.data(), hr.size() * sizeof(SegPiece), cudaMemcpyHostToDevice, s),
+            "upload heavy row pieces");
+        CKC(cudaMemsetAsync(h->row_cnt, 0, (size_t)nseg_r * 4, s), "clear heavy row counters");
+    }
+    if (!hc.empty()) {
+        CKC(cudaMemcpyAsync(h->col_pieces, hc.data(), hc.size() * sizeof(SegPiece), cudaMemcpyHostToDevice, s),
+            "upload heavy column pieces");
+        CKC(cudaMemsetAsync(h->col_cnt, 0, (size_t)nseg_c * 4, s), "clear heavy column counters");
+    }
 
     sp.rp = h->rp;
     sp.ci = h->ci;
@@ -756,8 +798,12 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     sp.ri = h->ri;
     sp.vc = h->vc;
     sp.meta = h->meta;
-    sp.heavy_rows = h->heavy_rows;
-    sp.heavy_cols = h->heavy_cols;
+    sp.row_pieces = h->row_pieces;
+    sp.col_pieces = h->col_pieces;
+    sp.row_slots = h->row_slots;
+    sp.col_slots = h->col_slots;
+    sp.row_cnt = h->row_cnt;
+    sp.col_cnt = h->col_cnt;
     sp.coef = h->coef;
     sp.x = h->x;
     sp.x64 = h->x64;

@@ -197,6 +197,16 @@ cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const
 // ---- sparse A (nsli_sparse.cu) ----------------------------------------------
 // A held as CSR (rows, for the residuals) and CSC (columns, for y), values
 // in the storage type (binary64 or binary32), indices int32, offsets int64.
+
+// One CTA's piece of a heavy row (column): entries [e0, e1) of segment seg,
+// piece k of npieces; the partial sums of the segment's pieces go to slots
+// first .. first + npieces - 1; hs indexes the segment's arrival counter.
+struct SegPiece {
+    int seg, hs, first, npieces, k, pad;
+    long long e0, e1;
+};
+constexpr int kSparsePiece = 2048;   // entries per heavy piece
+
 struct SparseArgs {
     const long long *rp;      // m + 1 row offsets
     const int *ci;            // nnz column indices, ascending within a row
@@ -205,8 +215,10 @@ struct SparseArgs {
     const int *ri;            // nnz row indices, ascending within a column
     const void *vc;           // nnz values in column order
     const void *meta;         // m row records (RowMeta32 / RowMeta64)
-    const int *heavy_rows;    // rows longer than heavy_thr_row, one CTA each
-    const int *heavy_cols;    // columns longer than heavy_thr_col
+    const SegPiece *row_pieces;  // pieces of rows longer than heavy_thr_row
+    const SegPiece *col_pieces;  // pieces of columns longer than heavy_thr_col
+    void *row_slots, *col_slots; // partial sums of the pieces (accumulation type)
+    int *row_cnt, *col_cnt;      // per heavy segment arrival counters (zero between launches)
     void *coef;               // m: max(r_i, 0) / ||a_i||^2, accumulation type
     void *x;                  // n, accumulation type
     double *x64;              // n, the binary64 iterate
@@ -217,12 +229,14 @@ struct SparseArgs {
     long long m, n;
     long long light_rows_per_cta, light_cols_per_cta;
     long long heavy_thr_row, heavy_thr_col;
-    int n_heavy_rows, n_heavy_cols;
+    int n_row_pieces, n_col_pieces;
     int row_light_ctas, col_light_ctas, step_ctas;
     int w_row, w_col;         // lanes per row / column (1, 2, 4, ..., 32)
     int ignore_done;          // run even when the done flag is set
     int mode;                 // 0: iteration; 1: Map and y only (no decision, no step)
 };
+// resident CTAs per SM of the row / column kernel instances for these widths
+void sparse_blocks_per_sm(bool f64, int w_row, int w_col, int *row_bps, int *col_bps);
 cudaError_t sparse_row_launch(bool f64, cudaStream_t s, const SparseArgs &a);
 cudaError_t sparse_col_launch(bool f64, cudaStream_t s, const SparseArgs &a);
 cudaError_t sparse_step_launch(bool f64, cudaStream_t s, const SparseArgs &a);

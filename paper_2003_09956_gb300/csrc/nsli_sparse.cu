@@ -17,9 +17,14 @@
 //                       in place, or y_j kept for ModAP; per-CTA sums of
 //                       dx^2 (or y^2) folded by the last CTA.
 //   sparse_step_kernel  ModAP only: x_j -= lambda y_j / ||y||.
-// Rows (columns) longer than a threshold are "heavy": one CTA each, at the
-// front of the grid; the other CTAs take fixed ranges of the rest with
-// sub-warp groups of W lanes per row (column).
+// Rows (columns) up to a length threshold are "light": fixed ranges of them
+// per CTA, W lanes per row, each lane issuing kU independent loads of
+// indices and entries (evict-first: they are read once per iteration), then
+// kU gathers of x (of the coefficients) from L2.  Longer ones are "heavy":
+// cut into pieces of kPiece entries, one CTA per piece at the front of the
+// grid; a piece stores its partial sum in a fixed slot and the last piece of
+// a row to finish (per-row counter) adds the slots in order, so the sums
+// stay independent of timing.
 #include <cstdint>
 
 #include "nsli.h"
@@ -29,6 +34,7 @@ namespace nsli {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kU = 4;                        // independent loads per lane per chunk
 
 template <typename T> struct SpTraits;
 template <> struct SpTraits<double> {
@@ -68,6 +74,66 @@ template <typename T> __device__ __forceinline__ T block_sum(T v, T *sh)
     for (int q = 0; q < kThreads / 32; ++q)
         t += sh[q];
     return t;
+}
+
+// sum over e in [e0, e1) of val[e] * g[idx[e]] for lane l of a group of W
+// lanes: chunks of W * kU entries, lane l taking e = c + l + u W, the kU
+// loads of a chunk issued before any of its products; lane-local order.
+template <typename T, int W>
+__device__ __forceinline__ T seg_dot(long long e0, long long e1, const int *idx, const T *val, const T *g, int l)
+{
+    T acc = T(0);
+    for (long long c = e0; c < e1; c += (long long)W * kU) {
+        int id[kU];
+        T v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const long long e = c + l + (long long)u * W;
+            const bool ok = e < e1;
+            id[u] = ok ? __ldcs(idx + e) : 0;
+            v[u] = ok ? __ldcs(val + e) : T(0);
+        }
+        T gv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            gv[u] = __ldg(g + id[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            acc = fma(v[u], gv[u], acc);
+    }
+    return acc;
+}
+
+// One piece of a heavy row / column: the block's sum over the piece, then
+// (pieces > 1) the slot write and the per-segment counter.  Returns true in
+// every thread when this block holds the finished segment sum in *total.
+template <typename T>
+__device__ __forceinline__ bool heavy_piece(const SegPiece &pc, const int *idx, const T *val, const T *g, T *slots,
+                                            int *cnt, T *sh_sum, int *sh_flag, T *total)
+{
+    const T acc = seg_dot<T, kThreads>(pc.e0, pc.e1, idx, val, g, threadIdx.x);
+    const T part = block_sum(acc, sh_sum);
+    if (pc.npieces == 1) {
+        *total = part;
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        slots[pc.first + pc.k] = part;
+        __threadfence();
+        const int old = atomicAdd(cnt + pc.hs, 1);
+        *sh_flag = (old == pc.npieces - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*sh_flag)
+        return false;
+    __threadfence();
+    T t = T(0);
+    for (int q = 0; q < pc.npieces; ++q)
+        t += __ldcg(slots + pc.first + q);
+    *total = t;
+    if (threadIdx.x == 0)
+        cnt[pc.hs] = 0;   // ready for the next launch
+    return true;
 }
 
 struct StatAcc {
@@ -181,25 +247,21 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
         return;
     __shared__ StatAcc sh_stat[kThreads / 32];
     __shared__ T sh_sum[kThreads / 32];
-    __shared__ int sh_last;
+    __shared__ int sh_last, sh_flag;
     const T *va = static_cast<const T *>(p.va);
     const T *x = static_cast<const T *>(p.x);
     const T tk = (T)((double)st->tick * st->rho);
     StatAcc s{0, -INFINITY, -INFINITY, 0.0};
-    const int nblk = p.n_heavy_rows + p.row_light_ctas;
+    const int nblk = p.n_row_pieces + p.row_light_ctas;
 
-    if ((int)blockIdx.x < p.n_heavy_rows) {
-        // a heavy row: the whole block, then a fixed-order block sum
-        const long long i = p.heavy_rows[blockIdx.x];
-        const long long e0 = p.rp[i], e1 = p.rp[i + 1];
-        T acc = T(0);
-        for (long long e = e0 + threadIdx.x; e < e1; e += kThreads)
-            acc = fma(va[e], __ldg(x + p.ci[e]), acc);
-        const T dot = block_sum(acc, sh_sum);
-        if (threadIdx.x == 0)
-            finish_row(p, i, dot, tk, s);
+    if ((int)blockIdx.x < p.n_row_pieces) {
+        const SegPiece pc = p.row_pieces[blockIdx.x];
+        T dot;
+        if (heavy_piece(pc, p.ci, va, x, static_cast<T *>(p.row_slots), p.row_cnt, sh_sum, &sh_flag, &dot) &&
+            threadIdx.x == 0)
+            finish_row(p, pc.seg, dot, tk, s);
     } else {
-        const long long b = blockIdx.x - p.n_heavy_rows;
+        const long long b = blockIdx.x - p.n_row_pieces;
         const long long r0 = b * p.light_rows_per_cta;
         const long long r1 = min(r0 + p.light_rows_per_cta, p.m);
         constexpr int groups = kThreads / W;
@@ -217,8 +279,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
                 valid = (e1 - e0) <= p.heavy_thr_row;
             }
             if (valid)
-                for (long long e = e0 + l; e < e1; e += W)
-                    acc = fma(va[e], __ldg(x + p.ci[e]), acc);
+                acc = seg_dot<T, W>(e0, e1, p.ci, va, x, l);
             const T dot = group_sum<W>(acc);
             if (valid && l == 0)
                 finish_row(p, i, dot, tk, s);
@@ -278,26 +339,23 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
         return;
     __shared__ T sh_sum[kThreads / 32];
     __shared__ double sh_d[kThreads / 32];
-    __shared__ int sh_last;
+    __shared__ int sh_last, sh_flag;
     const T *vc = static_cast<const T *>(p.vc);
     const T *coef = static_cast<const T *>(p.coef);
     const long long h = st->h;
     const int rule = st->rule;
     const double s_relaxed = h > 0 ? st->lambda / (double)h : 0.0;
-    const int nblk = p.n_heavy_cols + p.col_light_ctas;
+    const int nblk = p.n_col_pieces + p.col_light_ctas;
     double part = 0.0;
 
-    if ((int)blockIdx.x < p.n_heavy_cols) {
-        const long long j = p.heavy_cols[blockIdx.x];
-        const long long e0 = p.cp[j], e1 = p.cp[j + 1];
-        T acc = T(0);
-        for (long long e = e0 + threadIdx.x; e < e1; e += kThreads)
-            acc = fma(__ldg(coef + p.ri[e]), vc[e], acc);
-        const T y = block_sum(acc, sh_sum);
-        if (threadIdx.x == 0)
-            part = col_update(p, j, y, s_relaxed, rule);
+    if ((int)blockIdx.x < p.n_col_pieces) {
+        const SegPiece pc = p.col_pieces[blockIdx.x];
+        T y;
+        if (heavy_piece(pc, p.ri, vc, coef, static_cast<T *>(p.col_slots), p.col_cnt, sh_sum, &sh_flag, &y) &&
+            threadIdx.x == 0)
+            part = col_update(p, pc.seg, y, s_relaxed, rule);
     } else {
-        const long long b = blockIdx.x - p.n_heavy_cols;
+        const long long b = blockIdx.x - p.n_col_pieces;
         const long long c0 = b * p.light_cols_per_cta;
         const long long c1 = min(c0 + p.light_cols_per_cta, p.n);
         constexpr int groups = kThreads / W;
@@ -313,8 +371,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
                 valid = (e1 - e0) <= p.heavy_thr_col;
             }
             if (valid)
-                for (long long e = e0 + l; e < e1; e += W)
-                    acc = fma(__ldg(coef + p.ri[e]), vc[e], acc);
+                acc = seg_dot<T, W>(e0, e1, p.ri, vc, coef, l);
             const T y = group_sum<W>(acc);
             if (valid && l == 0)
                 part += col_update(p, j, y, s_relaxed, rule);
@@ -457,6 +514,38 @@ template <typename T> __global__ void sparse_rows_kernel(const SparseArgs p, lon
         out[r * p.n + p.ci[e]] = (double)va[e];
 }
 
+template <typename T> int blocks_per_sm_row(int w)
+{
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (w) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 1>, kThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 2>, kThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 4>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 8>, kThreads, 0); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 16>, kThreads, 0); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_row_kernel<T, 32>, kThreads, 0); break;
+    default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+template <typename T> int blocks_per_sm_col(int w)
+{
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (w) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 1>, kThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 2>, kThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 4>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 8>, kThreads, 0); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 16>, kThreads, 0); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sparse_col_kernel<T, 32>, kThreads, 0); break;
+    default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
 template <typename T> cudaError_t row_launch(int w, unsigned grid, cudaStream_t s, const SparseArgs &a)
 {
     switch (w) {
@@ -487,15 +576,21 @@ template <typename T> cudaError_t col_launch(int w, unsigned grid, cudaStream_t 
 
 }  // namespace
 
+void sparse_blocks_per_sm(bool f64, int w_row, int w_col, int *row_bps, int *col_bps)
+{
+    *row_bps = f64 ? blocks_per_sm_row<double>(w_row) : blocks_per_sm_row<float>(w_row);
+    *col_bps = f64 ? blocks_per_sm_col<double>(w_col) : blocks_per_sm_col<float>(w_col);
+}
+
 cudaError_t sparse_row_launch(bool f64, cudaStream_t s, const SparseArgs &a)
 {
-    const unsigned grid = (unsigned)(a.n_heavy_rows + a.row_light_ctas);
+    const unsigned grid = (unsigned)(a.n_row_pieces + a.row_light_ctas);
     return f64 ? row_launch<double>(a.w_row, grid, s, a) : row_launch<float>(a.w_row, grid, s, a);
 }
 
 cudaError_t sparse_col_launch(bool f64, cudaStream_t s, const SparseArgs &a)
 {
-    const unsigned grid = (unsigned)(a.n_heavy_cols + a.col_light_ctas);
+    const unsigned grid = (unsigned)(a.n_col_pieces + a.col_light_ctas);
     return f64 ? col_launch<double>(a.w_col, grid, s, a) : col_launch<float>(a.w_col, grid, s, a);
 }
 
@@ -526,6 +621,7 @@ cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const Spars
         sparse_verify_kernel<float><<<grid, kThreads, 0, s>>>(a, v);
     return cudaGetLastError();
 }
+
 
 cudaError_t sparse_rows_launch(bool f64, cudaStream_t s, const SparseArgs &a, long long row0, long long rows,
                                double *out)

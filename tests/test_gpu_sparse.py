@@ -77,12 +77,12 @@ def case(name):
         return workloads.sparse_system(3000, 500, 0, seed=2, lengths=g.integers(1, 40, 3000))
     if name == "short-rows":        # 3 per row, 2 lanes per row, 1 per column
         return workloads.sparse_system(5000, 2000, 3, seed=3)
-    if name == "heavy-rows":        # every 50th row longer than the per-CTA threshold
+    if name == "heavy-rows":        # every 50th row cut into two pieces
         L = np.full(400, 5)
         L[::50] = 2500
         return workloads.sparse_system(400, 3000, 0, seed=4, lengths=L)
-    if name == "heavy-cols":        # columns 0, 1 in every one of 2000 rows
-        return workloads.sparse_system(2000, 1500, 0, seed=5, lengths=g.integers(3, 12, 2000),
+    if name == "heavy-cols":        # columns 0, 1 in every one of 5000 rows (3 pieces each)
+        return workloads.sparse_system(5000, 1500, 0, seed=5, lengths=g.integers(3, 12, 5000),
                                        dense_cols=2)
     if name == "few-long-rows":     # m far below the SM count, long light rows
         return workloads.sparse_system(20, 50000, 2000, seed=6)
