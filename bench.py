@@ -74,6 +74,8 @@ def parse_args():
     ap.add_argument("--sparse", default="sparse-4194304x1048576x32",
                     help="sparse workload measured in the same run ('' for none)")
     ap.add_argument("--sparse-only", action="store_true", help="time only the sparse workload")
+    ap.add_argument("--matrix-updates", default="bf16",
+                    help="storage for the run that rewrites A before every iteration ('' for none)")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the serving stream measured in the same run (0: none)")
     ap.add_argument("--serving-only", action="store_true", help="time only the serving stream")
@@ -312,6 +314,45 @@ def time_sparse(nsli, torch, name, steps, warmup, peak):
             "max_viol_f64": mv, "generate_s": t_gen}
 
 
+def time_matrix_updates(nsli, torch, p, storage, w, steps, warmup, peak):
+    """Every iteration preceded by a rewrite of ALL rows of A from device
+    memory (a time-dependent matrix, c_u = (n + 1) m): two source matrices
+    alternate, so each step stores, norms and streams a different A."""
+    m, n = p["m"], p["n"]
+    stream = torch.cuda.Stream()
+    src = p["A"] if storage != "f64" else p["A"].astype(np.float64)
+    s = nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage, stream=stream.cuda_stream)
+    A0 = torch.from_numpy(p["A"]).cuda()
+    A1 = A0 * 1.001
+    torch.cuda.synchronize()
+    srcs = [A0, A1]
+    for k in range(warmup):
+        s.update_rows(0, srcs[k % 2])
+        s.iterate(1, rho=w["rho"])
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    e0.record(stream)
+    for k in range(steps):
+        s.update_rows(0, srcs[k % 2])
+        s.iterate(1, rho=w["rho"])
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = s.launch_count() - l0
+    s.close()
+    del A0, A1, srcs
+    torch.cuda.empty_cache()
+    eb = ELEM_BYTES[storage]
+    moved = m * n * 4 + m * n * eb + map_bytes(m, n, storage)   # source read, stored write, Map read
+    return {"workload": "dense %dx%d, all rows of A rewritten from device memory before every iteration, "
+                        "%s storage" % (m, n, storage),
+            "value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms, "bytes_per_step": moved,
+            "gbs": moved / (ms / 1e3) / 1e9, "frac_of_measured_hbm": moved / (ms / 1e3) / 1e9 / peak,
+            "gpu_launches": launches}
+
+
 SERVE = {"rate": 200.0, "tick_s": 0.010, "rho": 1e-4, "eps": 1e-6, "max_iter": 300, "seed": 2010,
          "classes": [int(round(512 * 2 ** (k / 2))) for k in range(11)], "c": [2, 4, 8]}
 
@@ -547,6 +588,9 @@ def main():
     variants["model_system_f64"] = time_model_system(nsli)
     if args.sparse:
         variants["sparse_f32"] = time_sparse(nsli, torch, args.sparse, K, W, peak)
+    if args.matrix_updates:
+        variants["matrix_rewrite_every_tick_" + args.matrix_updates] = time_matrix_updates(
+            nsli, torch, p, args.matrix_updates, w, min(K, 50), W, peak)
     if args.batched:
         variants["batched_bf16"] = time_batched(nsli, torch, args.batched, min(K, 100), W)
     if args.serve_seconds > 0 and world == 1:

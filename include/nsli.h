@@ -164,6 +164,28 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage,
  * Section 5: the data update step of each iteration. */
 int nsli_update_b(nsli_handle h, const double *b0, int64_t tick);
 
+/* Replace rows row0 .. row0 + rows - 1 of A (and optionally their b0)
+ * between iterations: the data update step of Section 3 for a system whose
+ * matrix changes with time (Eq. 1; Section 4 prices a full change at
+ * (n + 1) m values).  Issued on the handle's stream after the work already
+ * queued, so the next iteration sees the new rows.
+ *   a_dtype  NSLI_F32 or NSLI_F64: element type of the new rows (BF16 and
+ *            FP8E4M3 storage need NSLI_F32).
+ *   A        host or device, row-major, rows rows of lda elements
+ *            (lda >= n); row q replaces row row0 + q; copied, not retained.
+ *   b0       host or device, rows doubles: new right-hand sides at tick 0 of
+ *            the same rows, or NULL to keep them.
+ * The rows are stored, normed (binary64, from the stored values) and their
+ * records rebuilt exactly as nsli_create does.  A row that holds a NaN / Inf
+ * (or whose new b0 does) or is all zeros keeps its previous values; the call
+ * then returns NSLI_ERR_NONFINITE or NSLI_ERR_ZERO_ROW after updating the
+ * other rows.  Other errors: NSLI_ERR_ARG (range outside [0, m), NULL A,
+ * lda < n, dtype), NSLI_ERR_UNSUPPORTED (a sparse handle), NSLI_ERR_OOM /
+ * NSLI_ERR_CUDA.  Synchronises (it reads the row flags back). */
+int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows,
+                     int32_t a_dtype, const void *A, int64_t lda,
+                     const double *b0);
+
 /* Run exactly n_iter iterations (Map, Reduce, step, tick) with no stopping
  * test (p->stop is ignored); an iteration with h == 0 makes no step.  Issues
  * the work asynchronously on the handle's stream and returns without

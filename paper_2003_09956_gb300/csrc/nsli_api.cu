@@ -645,8 +645,8 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
         }
 
     // lanes per row / column from the median length (a few very long rows or
-    // columns do not set it): W lanes x 4 loads cover a typical one in one
-    // chunk; those needing more than 4 chunks are cut into pieces of
+    // columns do not set it): W lanes x kSparseU loads cover a typical one in
+    // one chunk; those needing more than 4 chunks are cut into pieces of
     // kSparsePiece entries, one CTA each
     auto median_len = [](const std::vector<long long> &off) {
         std::vector<long long> len(off.size() - 1);
@@ -657,7 +657,7 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     };
     auto pick_w = [](double typical) {
         int w = 1;
-        while (w < 32 && 4.0 * w < typical)
+        while (w < 32 && (double)kSparseU * w < typical)
             w *= 2;
         return w;
     };
@@ -693,8 +693,8 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     sp.n = n;
     sp.w_row = pick_w(median_len(rp));
     sp.w_col = pick_w(median_len(cp));
-    sp.heavy_thr_row = 16ll * sp.w_row;
-    sp.heavy_thr_col = 16ll * sp.w_col;
+    sp.heavy_thr_row = 4ll * kSparseU * sp.w_row;
+    sp.heavy_thr_col = 4ll * kSparseU * sp.w_col;
     std::vector<SegPiece> hr, hc;
     long long nseg_r = 0, nslot_r = 0, nseg_c = 0, nslot_c = 0;
     make_pieces(rp, sp.heavy_thr_row, hr, &nseg_r, &nslot_r);
@@ -893,6 +893,80 @@ int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
     if (b0)
         return read_flags(h);
     return NSLI_OK;
+}
+
+int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype, const void *A, int64_t lda,
+                     const double *b0)
+{
+    if (!h)
+        return NSLI_ERR_ARG;
+    if (h->sparse)
+        return set_err(h, NSLI_ERR_UNSUPPORTED, "rows of a sparse matrix are not replaced in place");
+    if (row0 < 0 || rows < 0 || row0 + rows > h->m || (rows > 0 && (!A || lda < h->n)))
+        return set_err(h, NSLI_ERR_ARG, "bad row range, source or lda");
+    if (a_dtype != NSLI_F32 && a_dtype != NSLI_F64)
+        return set_err(h, NSLI_ERR_ARG, "source must be binary32 or binary64");
+    if ((h->storage == NSLI_BF16 || h->storage == NSLI_FP8E4M3) && a_dtype != NSLI_F32)
+        return set_err(h, NSLI_ERR_ARG, "bf16 / fp8 storage needs a binary32 source");
+    if (rows == 0)
+        return NSLI_OK;
+    cudaStream_t s = h->stream;
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(int), s), "clear flags");
+    const size_t src_eb = a_dtype == NSLI_F64 ? 8 : 4;
+    const bool on_device = is_device_ptr(A);
+    // rows per launch: all of them for a device source, else a staged chunk
+    long long chunk = on_device ? rows : std::max<long long>(1, (256ll << 20) / (long long)(lda * src_eb));
+    chunk = std::min<long long>(chunk, rows);
+    void *stage = nullptr;
+    if (!on_device)
+        CK(cudaMalloc(&stage, (size_t)chunk * lda * src_eb), "allocate staging for rows");
+    cudaError_t err = cudaSuccess;
+    for (long long r0 = 0; r0 < rows && err == cudaSuccess; r0 += chunk) {
+        const long long cnt = std::min(chunk, rows - r0);
+        UpdateArgs ua;
+        if (on_device) {
+            ua.src = static_cast<const unsigned char *>(A) + (size_t)r0 * lda * src_eb;
+        } else {
+            err = cudaMemcpy2DAsync(stage, (size_t)lda * src_eb,
+                                    static_cast<const unsigned char *>(A) + (size_t)r0 * lda * src_eb,
+                                    (size_t)lda * src_eb, (size_t)h->n * src_eb, (size_t)cnt, cudaMemcpyDefault, s);
+            if (err != cudaSuccess)
+                break;
+            ua.src = stage;
+        }
+        ua.b0_new = nullptr;
+        if (b0) {
+            // the new right-hand sides go through the staging buffer (m doubles)
+            err = cudaMemcpyAsync(h->dtmp, b0 + r0, (size_t)cnt * 8, cudaMemcpyDefault, s);
+            if (err != cudaSuccess)
+                break;
+            ua.b0_new = h->dtmp;
+        }
+        ua.lda = lda;
+        ua.src_f64 = a_dtype == NSLI_F64 ? 1 : 0;
+        ua.A = h->A;
+        ua.ld = h->ld;
+        ua.n = h->n;
+        ua.row0 = row0 + r0;
+        ua.rows = cnt;
+        ua.b0_64 = h->b0_64;
+        ua.av_64 = h->av_64;
+        ua.n2_64 = h->n2_64;
+        ua.scale = h->scale;
+        ua.meta = h->meta;
+        ua.flags = h->flags;
+        err = update_rows_launch(h->storage, s, ua);
+        h->launches += 1;
+        if (err == cudaSuccess && (!on_device || b0) && r0 + cnt < rows)
+            err = cudaStreamSynchronize(s);  // staging buffers are reused
+    }
+    if (stage) {
+        if (err == cudaSuccess)
+            err = cudaStreamSynchronize(s);
+        cudaFree(stage);
+    }
+    CK(err, "update rows");
+    return read_flags(h);
 }
 
 int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)

@@ -165,6 +165,25 @@ struct PrepArgs {
 };
 cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a);
 
+// rows row0 .. row0 + rows - 1 replaced from src (device, pitch lda, binary32
+// or binary64); b0_new (device, rows values) or NULL keeps b0 (nsli_update.cu)
+struct UpdateArgs {
+    const void *src;
+    long long lda;
+    int src_f64;
+    void *A;
+    long long ld, n;
+    long long row0, rows;
+    const double *b0_new;
+    double *b0_64;
+    const double *av_64;
+    double *n2_64;
+    float *scale;
+    void *meta;
+    int *flags;
+};
+cudaError_t update_rows_launch(int storage, cudaStream_t s, const UpdateArgs &a);
+
 struct MetaArgs {
     void *meta;
     const double *b0_64, *av_64, *n2_64;
@@ -206,6 +225,10 @@ struct SegPiece {
     long long e0, e1;
 };
 constexpr int kSparsePiece = 2048;   // entries per heavy piece
+#ifndef NSLI_SPARSE_KU
+#define NSLI_SPARSE_KU 4
+#endif
+constexpr int kSparseU = NSLI_SPARSE_KU;  // independent loads per lane per chunk
 
 struct SparseArgs {
     const long long *rp;      // m + 1 row offsets

@@ -34,7 +34,7 @@ namespace nsli {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kU = 4;                        // independent loads per lane per chunk
+constexpr int kU = kSparseU;
 
 template <typename T> struct SpTraits;
 template <> struct SpTraits<double> {
@@ -169,10 +169,9 @@ __device__ StatAcc block_stats(StatAcc s, StatAcc *sh)
 
 // r_i from a finished dot; writes c_i and folds the row into the stats.
 template <typename T>
-__device__ __forceinline__ void finish_row(const SparseArgs &p, long long i, T dot, T tk, StatAcc &s)
+__device__ __forceinline__ void finish_row(const SparseArgs &p, long long i, T dot, T tk,
+                                           const typename SpTraits<T>::Meta &md, StatAcc &s)
 {
-    using Meta = typename SpTraits<T>::Meta;
-    const Meta md = static_cast<const Meta *>(p.meta)[i];
     const T bi = fma(tk, (T)md.av, (T)md.b0);
     const T ri = dot - bi;
     const bool viol = ri > T(0);
@@ -242,6 +241,7 @@ __device__ __forceinline__ bool last_block(DevState *st, int nblk, int *sh_last)
 
 template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_row_kernel(const SparseArgs p)
 {
+    using Meta = typename SpTraits<T>::Meta;
     DevState *st = p.st;
     if (!p.ignore_done && *(volatile int *)&st->done)
         return;
@@ -259,7 +259,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
         T dot;
         if (heavy_piece(pc, p.ci, va, x, static_cast<T *>(p.row_slots), p.row_cnt, sh_sum, &sh_flag, &dot) &&
             threadIdx.x == 0)
-            finish_row(p, pc.seg, dot, tk, s);
+            finish_row(p, pc.seg, dot, tk, static_cast<const Meta *>(p.meta)[pc.seg], s);
     } else {
         const long long b = blockIdx.x - p.n_row_pieces;
         const long long r0 = b * p.light_rows_per_cta;
@@ -273,16 +273,19 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
             T acc = T(0);
             bool valid = i < r1;
             long long e0 = 0, e1 = 0;
+            Meta md{};
             if (valid) {
                 e0 = p.rp[i];
                 e1 = p.rp[i + 1];
+                if (l == 0)
+                    md = static_cast<const Meta *>(p.meta)[i];   // in flight with the entries
                 valid = (e1 - e0) <= p.heavy_thr_row;
             }
             if (valid)
                 acc = seg_dot<T, W>(e0, e1, p.ci, va, x, l);
             const T dot = group_sum<W>(acc);
             if (valid && l == 0)
-                finish_row(p, i, dot, tk, s);
+                finish_row(p, i, dot, tk, md, s);
         }
     }
     const StatAcc t = block_stats(s, sh_stat);
@@ -313,7 +316,8 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
 
 // y_j = sum over the column's entries (rows ascending) of c_i a_ij.
 template <typename T>
-__device__ __forceinline__ double col_update(const SparseArgs &p, long long j, T y, double s_relaxed, int rule)
+__device__ __forceinline__ double col_update(const SparseArgs &p, long long j, T y, double s_relaxed, int rule,
+                                             double xo)
 {
     if (p.mode != 0) {
         p.ybuf[j] = (double)y;
@@ -324,7 +328,6 @@ __device__ __forceinline__ double col_update(const SparseArgs &p, long long j, T
         p.ybuf[j] = yd;
         return yd * yd;
     }
-    const double xo = p.x64[j];
     const double xn = xo - s_relaxed * (double)y;
     p.x64[j] = xn;
     static_cast<T *>(p.x)[j] = (T)xn;
@@ -353,7 +356,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
         T y;
         if (heavy_piece(pc, p.ri, vc, coef, static_cast<T *>(p.col_slots), p.col_cnt, sh_sum, &sh_flag, &y) &&
             threadIdx.x == 0)
-            part = col_update(p, pc.seg, y, s_relaxed, rule);
+            part = col_update(p, pc.seg, y, s_relaxed, rule, p.x64[pc.seg]);
     } else {
         const long long b = blockIdx.x - p.n_col_pieces;
         const long long c0 = b * p.light_cols_per_cta;
@@ -365,16 +368,19 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
             T acc = T(0);
             bool valid = j < c1;
             long long e0 = 0, e1 = 0;
+            double xo = 0.0;
             if (valid) {
                 e0 = p.cp[j];
                 e1 = p.cp[j + 1];
+                if (l == 0 && p.mode == 0 && rule != NSLI_RULE_MODAP)
+                    xo = p.x64[j];   // in flight with the entries
                 valid = (e1 - e0) <= p.heavy_thr_col;
             }
             if (valid)
                 acc = seg_dot<T, W>(e0, e1, p.ri, vc, coef, l);
             const T y = group_sum<W>(acc);
             if (valid && l == 0)
-                part += col_update(p, j, y, s_relaxed, rule);
+                part += col_update(p, j, y, s_relaxed, rule, xo);
         }
     }
     const double bsum = block_sum(part, sh_d);

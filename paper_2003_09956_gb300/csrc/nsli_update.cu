@@ -1,0 +1,199 @@
+// nsli_update.cu -- replacing rows of A between iterations (the data update
+// step of the method on lists, Section 3, for a system whose matrix changes
+// with time, Eq. 1; Section 4 prices a full change at (n + 1) m values).
+//
+// One block per updated row.  Pass 1 reads the new row (binary32 or
+// binary64 source), takes the FP8 row scale where needed, and sums the
+// squares of the values as they will be STORED, in binary64, in the same
+// order as the set-up kernel (so a row gets the same norm whether it came
+// with nsli_create or with an update).  A row that is not finite or is all
+// zeros is left as it was and flagged; otherwise pass 2 (the row is in L2
+// by then) writes the stored values, its norm, the new b0 if one was given,
+// and the row record.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cmath>
+
+#include "nsli.h"
+#include "nsli_internal.h"
+
+namespace nsli {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int S> __device__ __forceinline__ double stored_value(const void *src, bool f64src, long long j,
+                                                                float inv_scale, float scale, bool *bad)
+{
+    if (S == NSLI_F64) {
+        const double v = f64src ? static_cast<const double *>(src)[j] : (double)static_cast<const float *>(src)[j];
+        if (!isfinite(v))
+            *bad = true;
+        return v;
+    } else if (S == NSLI_F32) {
+        float v;
+        if (f64src) {
+            const double d = static_cast<const double *>(src)[j];
+            if (!isfinite(d))
+                *bad = true;
+            v = __double2float_rn(d);
+        } else {
+            v = static_cast<const float *>(src)[j];
+            if (!isfinite(v))
+                *bad = true;
+        }
+        return (double)v;
+    } else if (S == NSLI_BF16) {
+        const float a = static_cast<const float *>(src)[j];
+        if (!isfinite(a))
+            *bad = true;
+        return (double)__bfloat162float(__float2bfloat16_rn(a));
+    } else {
+        const float a = static_cast<const float *>(src)[j];
+        if (!isfinite(a))
+            *bad = true;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        return (double)__half2float(__half(hr)) * (double)scale;
+    }
+}
+
+template <int S> __device__ __forceinline__ void store_value(void *A, long long at, const void *src, bool f64src,
+                                                             long long j, bool in, float inv_scale)
+{
+    if (S == NSLI_F64) {
+        const double v = in ? (f64src ? static_cast<const double *>(src)[j]
+                                      : (double)static_cast<const float *>(src)[j])
+                            : 0.0;
+        static_cast<double *>(A)[at] = v;
+    } else if (S == NSLI_F32) {
+        const float v = in ? (f64src ? __double2float_rn(static_cast<const double *>(src)[j])
+                                     : static_cast<const float *>(src)[j])
+                           : 0.0f;
+        static_cast<float *>(A)[at] = v;
+    } else if (S == NSLI_BF16) {
+        const float a = in ? static_cast<const float *>(src)[j] : 0.0f;
+        static_cast<__nv_bfloat16 *>(A)[at] = __float2bfloat16_rn(a);
+    } else {
+        const float a = in ? static_cast<const float *>(src)[j] : 0.0f;
+        static_cast<unsigned char *>(A)[at] =
+            (unsigned char)__nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(const UpdateArgs p)
+{
+    const long long r = blockIdx.x;
+    if (r >= p.rows)
+        return;
+    const long long gi = p.row0 + r;
+    __shared__ double sred[kThreads / 32];
+    __shared__ float samax[kThreads / 32];
+    __shared__ int sbad;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        sbad = 0;
+    __syncthreads();
+    const size_t eb = p.src_f64 ? 8 : 4;
+    const void *src = static_cast<const unsigned char *>(p.src) + (size_t)r * p.lda * eb;
+    bool bad = false;
+
+    float scale = 1.0f, inv_scale = 1.0f;
+    if (S == NSLI_FP8E4M3) {
+        float amax = 0.0f;
+        for (long long j = threadIdx.x; j < p.n; j += kThreads)
+            amax = fmaxf(amax, fabsf(static_cast<const float *>(src)[j]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        if (lane == 0)
+            samax[wid] = amax;
+        __syncthreads();
+        amax = 0.0f;
+        for (int q = 0; q < kThreads / 32; ++q)
+            amax = fmaxf(amax, samax[q]);
+        int e = 0;
+        if (amax > 0.0f && isfinite(amax)) {
+            int e2;
+            const float f = frexpf(amax, &e2);   // amax = f 2^e2, f in [0.5, 1)
+            e = (f <= 0.875f) ? e2 - 9 : e2 - 8; // smallest 2^e with amax / 2^e <= 448
+        }
+        scale = ldexpf(1.0f, e);
+        inv_scale = ldexpf(1.0f, -e);
+    }
+
+    // pass 1: norm of the stored values (same order as the set-up kernel)
+    double n2 = 0.0;
+    for (long long j = threadIdx.x; j < p.ld; j += kThreads) {
+        if (j < p.n) {
+            const double v = stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad);
+            n2 += v * v;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+    if (bad)
+        sbad = 1;
+    if (lane == 0)
+        sred[wid] = n2;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q)
+        t += sred[q];
+    const double b_new = p.b0_new ? p.b0_new[r] : 0.0;
+    int f = 0;
+    if (sbad || !isfinite(t) || (p.b0_new && !isfinite(b_new)))
+        f |= PREPF_NONFINITE;
+    else if (t == 0.0)
+        f |= PREPF_ZERO_ROW;
+    if (f) {
+        if (threadIdx.x == 0)
+            atomicOr(p.flags, f);
+        return;   // the row keeps its previous values
+    }
+
+    // pass 2: store (zero padding up to ld), then the row's norm and record
+    for (long long j = threadIdx.x; j < p.ld; j += kThreads)
+        store_value<S>(p.A, gi * p.ld + j, src, p.src_f64 != 0, j, j < p.n, inv_scale);
+    if (threadIdx.x == 0) {
+        p.n2_64[gi] = t;
+        if (p.b0_new)
+            p.b0_64[gi] = b_new;
+        const double b0 = p.b0_new ? b_new : p.b0_64[gi];
+        const double av = p.av_64[gi];
+        const double inv_n2 = 1.0 / t;
+        const double inv_n = 1.0 / sqrt(t);
+        if (S == NSLI_F64) {
+            RowMeta64 m{b0, av, inv_n2, inv_n};
+            static_cast<RowMeta64 *>(p.meta)[gi] = m;
+        } else {
+            if (S == NSLI_FP8E4M3)
+                p.scale[gi] = scale;
+            RowMeta32 m{(float)b0, (float)av, (float)inv_n2, (float)inv_n,
+                        (S == NSLI_FP8E4M3) ? scale : 1.0f, 0.0f, 0.0f, 0.0f};
+            static_cast<RowMeta32 *>(p.meta)[gi] = m;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t update_rows_launch(int storage, cudaStream_t s, const UpdateArgs &a)
+{
+    if (a.rows <= 0)
+        return cudaSuccess;
+    const unsigned grid = (unsigned)a.rows;
+    switch (storage) {
+    case NSLI_F64: update_rows_kernel<NSLI_F64><<<grid, kThreads, 0, s>>>(a); break;
+    case NSLI_F32: update_rows_kernel<NSLI_F32><<<grid, kThreads, 0, s>>>(a); break;
+    case NSLI_BF16: update_rows_kernel<NSLI_BF16><<<grid, kThreads, 0, s>>>(a); break;
+    case NSLI_FP8E4M3: update_rows_kernel<NSLI_FP8E4M3><<<grid, kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nsli

@@ -61,7 +61,7 @@ class NsliError(RuntimeError):
 
 _lib = None
 _lock = threading.Lock()
-EXPORTS = ["nsli_create", "nsli_create_csr", "nsli_update_b", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
+EXPORTS = ["nsli_create", "nsli_create_csr", "nsli_update_b", "nsli_update_rows", "nsli_iterate", "nsli_iterate_timed", "nsli_solve",
            "nsli_residual_max", "nsli_map_reduce", "nsli_get_x", "nsli_set_x",
            "nsli_get_stored_rows", "nsli_get_norms2", "nsli_test_inject_timeout",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
@@ -97,6 +97,8 @@ def load(path: str | None = None):
         lib.nsli_create.restype = ctypes.c_int
         lib.nsli_create_csr.argtypes = [ctypes.POINTER(H), i64, i64, i32, i64, P, P, P, P, P, P, P, P]
         lib.nsli_create_csr.restype = ctypes.c_int
+        lib.nsli_update_rows.argtypes = [H, i64, i64, i32, P, i64, P]
+        lib.nsli_update_rows.restype = ctypes.c_int
         lib.nsli_update_b.argtypes = [H, P, i64]
         lib.nsli_update_b.restype = ctypes.c_int
         lib.nsli_iterate.argtypes = [H, ctypes.POINTER(nsli_params), i64]
@@ -319,6 +321,25 @@ class Solver:
         b0 = _f64(b0, self.m)
         _sync_torch_inputs(b0)
         _check(load().nsli_update_b(self._h, _ptr(b0), int(tick)), "nsli_update_b", self._h)
+
+    def update_rows(self, row0, A_rows, b0=None):
+        """Replace rows row0 .. row0 + len(A_rows) - 1 (and their b0)."""
+        if isinstance(A_rows, np.ndarray):
+            if A_rows.dtype not in (np.float32, np.float64):
+                A_rows = A_rows.astype(np.float32)
+            A_rows = np.ascontiguousarray(A_rows)
+            a_dtype = F64 if A_rows.dtype == np.float64 else F32
+        else:
+            import torch
+            if A_rows.dtype not in (torch.float32, torch.float64):
+                A_rows = A_rows.to(torch.float32)
+            A_rows = A_rows.contiguous()
+            a_dtype = F64 if A_rows.dtype == torch.float64 else F32
+        rows, lda = int(A_rows.shape[0]), int(A_rows.shape[1])
+        b0 = _f64(b0, rows)
+        _sync_torch_inputs(A_rows, b0)
+        _check(load().nsli_update_rows(self._h, int(row0), rows, a_dtype, _ptr(A_rows), lda, _ptr(b0)),
+               "nsli_update_rows", self._h)
 
     def iterate(self, n_iter, lam=1.0, rule="relaxed", rho=0.0, block_iters=0):
         p = make_params(lam=lam, rule=rule, rho=rho, block_iters=block_iters)

@@ -261,3 +261,11 @@ def csr_to_dense(rp: np.ndarray, ci: np.ndarray, val: np.ndarray, n: int) -> np.
     rows = np.repeat(np.arange(m), np.diff(rp))
     A[rows, ci] = val
     return A
+
+
+def drifted_matrix(A0: np.ndarray, k: int, seed: int, amp: float = 0.05) -> np.ndarray:
+    """A(k) = A0 + amp G_k, G_k ~ N(0, 1) drawn for tick k, rounded to
+    binary32: a matrix whose every entry changes at every tick (Eq. 1 with a
+    time-dependent A)."""
+    G = gaussian_matrix(A0.shape[0], A0.shape[1], seed * 1000003 + k)
+    return (A0.astype(np.float32) + np.float32(amp) * G).astype(np.float32)

@@ -1,0 +1,124 @@
+"""Rows of A replaced between iterations (a time-dependent matrix, Eq. 1;
+the data update step of Section 3) against the FP64 oracle through the C
+ABI: stored values, norms and records of the new rows, one-step parity,
+trajectories with the whole matrix changing at every tick, per-row
+rejection of invalid rows."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_09956_gb300 import nsli, workloads
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = ["f64", "f32", "bf16", "fp8"]
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    from paper_2003_09956_gb300 import _build
+    _build.build()
+    nsli.load()
+
+
+def stored_values(A32, storage):
+    if storage == "bf16":
+        return oracle.quantize_bf16(A32)
+    if storage == "fp8":
+        q, _ = oracle.quantize_e4m3_rows(A32)
+        return q
+    return A32
+
+
+def src(A32, storage):
+    return A32.astype(np.float64) if storage == "f64" else A32
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_updated_rows_equal_created_rows(storage):
+    """A handle created on A and updated to A' row block by row block (host
+    and device sources, with new b0) holds exactly what a handle created on
+    A' holds: stored values, norms, and one Map/Reduce."""
+    import torch
+    m, n = 1500, 700
+    p = workloads.dense_system(m, n, seed=61)
+    q = workloads.dense_system(m, n, seed=62)
+    with nsli.Solver(src(p["A"], storage), p["b0"], p["x0"], Av=p["Av"], storage=storage) as s, \
+            nsli.Solver(src(q["A"], storage), q["b0"], p["x0"], Av=p["Av"], storage=storage) as t:
+        s.update_rows(0, src(q["A"][:600], storage), b0=q["b0"][:600])             # host rows
+        dev = torch.from_numpy(src(q["A"][600:], storage)).cuda()
+        s.update_rows(600, dev, b0=torch.from_numpy(q["b0"][600:]).cuda())      # device rows
+        np.testing.assert_array_equal(s.stored_rows(), t.stored_rows())
+        np.testing.assert_array_equal(s.stored_rows(), stored_values(q["A"], storage).astype(np.float64))
+        np.testing.assert_array_equal(s.norms2(), t.norms2())
+        ys, hs, sts = s.map_reduce()
+        yt, ht, stt = t.map_reduce()
+        np.testing.assert_array_equal(ys, yt)
+        assert hs == ht and sts == stt
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_trajectory_with_matrix_changing_every_tick(storage):
+    """Every entry of A changes before every iteration (c_u = (n + 1) m,
+    Section 4): iterates match the oracle run on the same A(k) sequence."""
+    m, n, K = 900, 240, 10
+    p = workloads.dense_system(m, n, seed=63)
+    tol = 1e-12 if storage == "f64" else 1e-5
+    x = p["x0"].copy()
+    compared = 0
+    with nsli.Solver(src(p["A"], storage), p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+        for k in range(K):
+            Ak = workloads.drifted_matrix(p["A"], k, seed=64)
+            s.update_rows(0, src(Ak, storage))
+            A64 = Ak.astype(np.float64)
+            n2, _ = oracle.norms2(A64)
+            np.testing.assert_allclose(s.norms2(), n2, rtol=1e-13)
+            code, x_next, st, y, r = oracle.iteration(A64, p["b0"], p["Av"], 1e-3, k, n2, x)
+            xg = s.get_x()
+            drift = np.linalg.norm(xg - x)
+            u = 2.0 ** -53 if storage == "f64" else 2.0 ** -24
+            bound = 64 * u * (np.abs(A64) @ np.abs(x) + np.abs(p["b0"]) + 1.0) + np.sqrt(n2) * drift * 1.01
+            if np.any(np.abs(r) <= bound):
+                break
+            s.iterate(1, rho=1e-3)
+            x = x_next
+            rel = np.linalg.norm(s.get_x() - x) / np.linalg.norm(x)
+            assert rel <= tol, (k, rel)
+            compared += 1
+    assert compared >= 3
+
+
+def test_invalid_rows_are_rejected_one_by_one():
+    m, n = 300, 50
+    p = workloads.dense_system(m, n, seed=65)
+    new = workloads.dense_system(m, n, seed=66)["A"][:10].copy()
+    new[3, 7] = np.nan
+    new[5, :] = 0.0
+    with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"]) as s:
+        before = s.stored_rows()
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_rows(20, new)
+        assert e.value.code in (nsli.ERR_NONFINITE, nsli.ERR_ZERO_ROW)
+        after = s.stored_rows()
+        for q in range(10):
+            want = before[20 + q] if q in (3, 5) else new[q].astype(np.float64)
+            np.testing.assert_array_equal(after[20 + q], want)
+        np.testing.assert_array_equal(after[:20], before[:20])
+        np.testing.assert_array_equal(after[30:], before[30:])
+        # the handle still iterates on the valid system
+        s.iterate(3)
+        assert np.all(np.isfinite(s.get_x()))
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_rows(5, new[5:6])
+        assert e.value.code == nsli.ERR_ZERO_ROW
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_rows(295, new[:10])
+        assert e.value.code == nsli.ERR_ARG
+
+
+def test_update_rows_on_sparse_handle_unsupported():
+    p = workloads.sparse_system(100, 40, 4, seed=67)
+    with nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"]) as s:
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_rows(0, np.ones((1, 40), np.float32))
+        assert e.value.code == nsli.ERR_UNSUPPORTED
