@@ -23,6 +23,7 @@ namespace nsli {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = 8;   // independent loads per thread per step
 
 template <int S> __device__ __forceinline__ double stored_value(const void *src, bool f64src, long long j,
                                                                 float inv_scale, float scale, bool *bad)
@@ -103,8 +104,17 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     float scale = 1.0f, inv_scale = 1.0f;
     if (S == NSLI_FP8E4M3) {
         float amax = 0.0f;
-        for (long long j = threadIdx.x; j < p.n; j += kThreads)
-            amax = fmaxf(amax, fabsf(static_cast<const float *>(src)[j]));
+        for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
+            float a[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const long long j = j0 + (long long)u * kThreads;
+                a[u] = j < p.n ? fabsf(static_cast<const float *>(src)[j]) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                amax = fmaxf(amax, a[u]);
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
             amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
@@ -124,13 +134,19 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
         inv_scale = ldexpf(1.0f, -e);
     }
 
-    // pass 1: norm of the stored values (same order as the set-up kernel)
+    // pass 1: norm of the stored values (same order as the set-up kernel:
+    // thread t adds j = t, t + 256, ... in turn); kUnroll loads in flight
     double n2 = 0.0;
-    for (long long j = threadIdx.x; j < p.ld; j += kThreads) {
-        if (j < p.n) {
-            const double v = stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad);
-            n2 += v * v;
+    for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
+        double v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long j = j0 + (long long)u * kThreads;
+            v[u] = j < p.n ? stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0;
         }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            n2 += v[u] * v[u];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -156,8 +172,14 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     }
 
     // pass 2: store (zero padding up to ld), then the row's norm and record
-    for (long long j = threadIdx.x; j < p.ld; j += kThreads)
-        store_value<S>(p.A, gi * p.ld + j, src, p.src_f64 != 0, j, j < p.n, inv_scale);
+    for (long long j0 = threadIdx.x; j0 < p.ld; j0 += (long long)kThreads * kUnroll) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long j = j0 + (long long)u * kThreads;
+            if (j < p.ld)
+                store_value<S>(p.A, gi * p.ld + j, src, p.src_f64 != 0, j, j < p.n, inv_scale);
+        }
+    }
     if (threadIdx.x == 0) {
         p.n2_64[gi] = t;
         if (p.b0_new)
