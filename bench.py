@@ -39,6 +39,11 @@ WORKLOADS = {
     # the benchmark's row length on a quarter of the rows (2 GiB binary32):
     # larger than L2, small enough for profiler replays
     "dense-32768x16384": {"m": 32768, "n": 16384, "rho": 1e-4, "seed": 2006},
+    # rows longer than the register-resident limit (the chunked long-row Map):
+    # the paper's n = 54000 with m = 2n + 1 rows, and a 16384-row slice of that
+    # row length for profiler captures (3.5 GB binary32, larger than L2)
+    "dense-108001x54000": {"m": 108001, "n": 54000, "rho": 1e-4, "seed": 2013},
+    "dense-16384x54000": {"m": 16384, "n": 54000, "rho": 1e-4, "seed": 2014},
 }
 ELEM_BYTES = {"f32": 4, "bf16": 2, "fp8": 1, "f64": 8}
 BATCHED = {

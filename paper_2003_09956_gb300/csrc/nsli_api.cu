@@ -145,14 +145,28 @@ int choose_config(nsli_solver *h)
         }
     }
     if (h->vpt == 0) {
-        // long rows: the chunked two-pass kernel (no shared-memory ring)
+        // long rows: the chunked two-pass kernel (no shared-memory ring).
+        // R = rows per group: the largest of 4, 2, 1 whose rows, over all
+        // CTAs, take at most 160 MB between the two passes (measured at
+        // n = 54000: four rows per group beat fewer even where part of them
+        // must come back from DRAM); the partial-sum row goes to shared
+        // memory when it fits in 220 KB.
         h->consumers = 512;
         h->guard = true;
-        h->R = 1;
         h->nstage = 0;
         h->stage_stride = 0;
-        h->smem = 0;
         h->G = (int)std::min<long long>(h->num_sms, h->m);
+        long long budget = 160ll << 20;   // NSLI_LONG_L2_MB (8..512) overrides it
+        if (const char *env = std::getenv("NSLI_LONG_L2_MB")) {
+            const long long mb = std::atoll(env);
+            if (mb >= 8 && mb <= 512)
+                budget = mb << 20;
+        }
+        h->R = 4;
+        while (h->R > 1 && (long long)h->G * h->R * h->row_bytes > budget)
+            h->R /= 2;
+        const size_t ybytes = (size_t)h->ld * (h->storage == NSLI_F64 ? 8 : 4);
+        h->smem = ybytes <= 220 * 1024 ? ybytes : 0;
         h->rows_base = h->m / h->G;
         h->rows_rem = (int)(h->m % h->G);
         h->red_grid = (int)((h->ld + kReduceCols - 1) / kReduceCols);

@@ -23,6 +23,7 @@
 
 #include "nsli.h"
 #include "nsli_internal.h"
+#include "nsli_sumsq.cuh"
 
 namespace nsli {
 
@@ -536,32 +537,52 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_group_kernel(const Gr
 // --------------------------------------------------- Map, long rows --------
 //
 // Rows longer than the register-resident limit (n > 16384 for 4-, 2- and
-// 1-byte storage, n > 8192 for binary64).  The CTA takes its rows four at a
-// time and walks them in column chunks of 1024 16-byte vectors: thread t
-// owns vectors t and t + 512 of every chunk.  Pass 1 streams the chunk of
-// the four rows from HBM with 16-byte loads and accumulates the dots against
-// the chunk of x (loaded once per four rows); one block reduction gives the
-// four residuals.  Pass 2 re-reads the chunks of the violated rows (now in
-// L2) and adds r_i / ||a_i||^2 * a_i into the CTA's row of partial sums in
-// global memory, each thread its own columns (no atomics, a fixed order).
+// 1-byte storage, n > 8192 for binary64).  The CTA takes its rows RG at a
+// time and walks them in column chunks of 512 * 8 / RG 16-byte vectors:
+// thread t owns vectors t, t + 512, ... of every chunk.  Pass 1 streams the chunk of
+// the RG rows from HBM with 16-byte loads and accumulates the dots against
+// the chunk of x (loaded once per group, 16 bytes at a time); one block
+// reduction gives the RG residuals.  A thread owns 8 / RG vectors per chunk,
+// so every thread has 8 row vectors in flight whatever RG is.  Pass 2 re-reads the chunks of the violated rows and adds
+// r_i / ||a_i||^2 * a_i into the CTA's row of partial sums, each thread its
+// own columns (no atomics, a fixed order).  The host picks RG (4, 2 or 1) so
+// that the rows of a group, over all CTAs, stay within a budget of L2 until
+// pass 2 re-reads them, and keeps the partial sums in shared memory (SY)
+// when a row of them fits there; otherwise they live in global memory.
 constexpr int kLongThreads = 512;
-constexpr int kLongVPT = 2;
-constexpr int kLongRows = 4;
 
-template <int S>
+// x entries of one 16-byte vector of A, loaded 16 bytes at a time
+template <typename Acc, int EPV> __device__ __forceinline__ void load_x_vec(const Acc *xg, long long j, Acc (&xv)[EPV])
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(xg + j * EPV);
+    constexpr int NQ = EPV * (int)sizeof(Acc) / 16;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 w = __ldg(src + q);
+        const Acc *a = reinterpret_cast<const Acc *>(&w);
+#pragma unroll
+        for (int e = 0; e < 16 / (int)sizeof(Acc); ++e)
+            xv[q * (16 / (int)sizeof(Acc)) + e] = a[e];
+    }
+}
+
+template <int S, int RG, bool SY>
 __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs p)
 {
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
     constexpr int EPV = Tr::EPV;
-    constexpr int RG = kLongRows;
     constexpr int W = 32 / RG;
+    // vectors per thread per chunk: 8 row vectors in flight per thread
+    // whatever the group size
+    constexpr int kLongVPT = 8 / RG;
 
     DevState *st = p.st;
     if (!p.ignore_done && *(volatile int *)&st->done)
         return;
     __shared__ Acc red[2][RG][32];
+    extern __shared__ __align__(16) unsigned char long_smem[];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwarps = kLongThreads / 32;
@@ -574,7 +595,8 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
     const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
     const Meta *meta = static_cast<const Meta *>(p.meta);
     const Acc *xg = static_cast<const Acc *>(p.x);
-    Acc *py = static_cast<Acc *>(p.part_y) + b * p.ld;
+    Acc *py_g = static_cast<Acc *>(p.part_y) + b * p.ld;
+    Acc *py = SY ? reinterpret_cast<Acc *>(long_smem) : py_g;
     for (long long e = tid; e < p.ld; e += kLongThreads)
         py[e] = Acc(0);
     const Acc tk = (Acc)((double)st->tick * st->rho);
@@ -605,9 +627,13 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
                     q[rr][v] = (ok[v] && rr < gr)
                                    ? __ldg(reinterpret_cast<const uint4 *>(Ab + (r0 + rr) * (long long)p.row_bytes) + j[v])
                                    : make_uint4(0u, 0u, 0u, 0u);
+                if (ok[v]) {
+                    load_x_vec<Acc, EPV>(xg, j[v], xv[v]);
+                } else {
 #pragma unroll
-                for (int e = 0; e < EPV; ++e)
-                    xv[v][e] = ok[v] ? __ldg(xg + j[v] * EPV + e) : Acc(0);
+                    for (int e = 0; e < EPV; ++e)
+                        xv[v][e] = Acc(0);
+                }
             }
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr) {
@@ -691,6 +717,12 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
         }
         ++grp_counter;
     }
+    if (SY) {
+        // each thread wrote only its own columns; the copy-out mixes them
+        __syncthreads();
+        for (long long e = tid; e < p.ld; e += kLongThreads)
+            py_g[e] = py[e];
+    }
     if (tid == 0) {
         PartStat ps;
         ps.h = h_loc;
@@ -698,6 +730,27 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
         ps.maxnorm = (double)mn;
         ps.maxb = (double)mb;
         p.part_stat[b] = ps;
+    }
+}
+
+template <int S, int RG, bool SY> const void *long_fn_rg() { return (const void *)map_long_kernel<S, RG, SY>; }
+template <int S> const void *long_fn_s(int rg, bool sy)
+{
+    if (sy)
+        return rg == 4 ? long_fn_rg<S, 4, true>() : (rg == 2 ? long_fn_rg<S, 2, true>() : long_fn_rg<S, 1, true>());
+    return rg == 4 ? long_fn_rg<S, 4, false>() : (rg == 2 ? long_fn_rg<S, 2, false>() : long_fn_rg<S, 1, false>());
+}
+// the long-row instance for a storage type, rows per group and y placement
+const void *long_fn(int storage, int rg, bool sy)
+{
+    if (rg != 1 && rg != 2 && rg != 4)
+        return nullptr;
+    switch (storage) {
+    case NSLI_F64: return long_fn_s<NSLI_F64>(rg, sy);
+    case NSLI_F32: return long_fn_s<NSLI_F32>(rg, sy);
+    case NSLI_BF16: return long_fn_s<NSLI_BF16>(rg, sy);
+    case NSLI_FP8E4M3: return long_fn_s<NSLI_FP8E4M3>(rg, sy);
+    default: return nullptr;
     }
 }
 
@@ -1045,7 +1098,11 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
             p.scale[gi] = scale;
     }
 
+    // ||a_i||^2 of the stored values: binary64 for binary64 storage, else the
+    // double-float accumulation of nsli_sumsq.cuh (same order as the
+    // row-update kernel)
     double n2 = 0.0;
+    SumSq sq = sumsq_init();
     for (long long j = threadIdx.x; j < p.ld; j += blockDim.x) {
         const bool in = j < p.n;
         if (S == NSLI_F64) {
@@ -1059,24 +1116,29 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
             if (in && !(p.src_f64 ? isfinite(s64[j]) : isfinite(v)))
                 bad = 1;
             static_cast<float *>(p.A)[gi * p.ld + j] = v;
-            n2 += (double)v * (double)v;
+            if (in && isfinite(v))
+                sumsq_add(sq, v);
         } else if (S == NSLI_BF16) {
             const float a = in ? s32[j] : 0.0f;
             if (in && !isfinite(a))
                 bad = 1;
             const __nv_bfloat16 q = __float2bfloat16_rn(a);
             static_cast<__nv_bfloat16 *>(p.A)[gi * p.ld + j] = q;
-            const double v = (double)__bfloat162float(q);
-            n2 += v * v;
+            const float v = __bfloat162float(q);
+            if (in && isfinite(v))
+                sumsq_add(sq, v);
         } else {
             const float a = in ? s32[j] : 0.0f;
             const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
             static_cast<unsigned char *>(p.A)[gi * p.ld + j] = (unsigned char)q;
             const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
-            const double v = (double)__half2float(__half(hr)) * (double)scale;
-            n2 += v * v;
+            const float v = __fmul_rn(__half2float(__half(hr)), scale);   // exact: scale is a power of two
+            if (in)
+                sumsq_add(sq, v);
         }
     }
+    if (S != NSLI_F64)
+        n2 = sumsq_value(sq);
     n2 = warp_sum(n2);
     if (bad)
         sbad = 1;
@@ -1249,8 +1311,20 @@ static const void *map_fn_any(int storage, int vpt, bool guard)
 
 cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
 {
-    if (vpt == 0)
-        return cudaSuccess;  // long rows: static shared memory only
+    if (vpt == 0) {
+        // long rows: partial sums in shared memory for every group size
+        if (smem == 0)
+            return cudaSuccess;
+        for (int rg = 1; rg <= 4; rg *= 2) {
+            const void *fn = long_fn(storage, rg, true);
+            if (!fn)
+                return cudaErrorInvalidValue;
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return e;
+        }
+        return cudaSuccess;
+    }
     const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)
         return cudaErrorInvalidValue;
@@ -1261,14 +1335,13 @@ cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers
                        const MapArgs &a)
 {
     if (vpt == 0) {
-        switch (storage) {
-        case NSLI_F64: map_long_kernel<NSLI_F64><<<grid, kLongThreads, 0, s>>>(a); break;
-        case NSLI_F32: map_long_kernel<NSLI_F32><<<grid, kLongThreads, 0, s>>>(a); break;
-        case NSLI_BF16: map_long_kernel<NSLI_BF16><<<grid, kLongThreads, 0, s>>>(a); break;
-        case NSLI_FP8E4M3: map_long_kernel<NSLI_FP8E4M3><<<grid, kLongThreads, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
+        // long rows: rows_per_slot carries the group size, smem the
+        // partial-sum row in shared memory (0: in global memory)
+        const void *fn = long_fn(storage, a.rows_per_slot, smem > 0);
+        if (!fn)
+            return cudaErrorInvalidValue;
+        void *args[] = {const_cast<MapArgs *>(&a)};
+        return cudaLaunchKernel(fn, dim3(grid), dim3(kLongThreads), args, smem, s);
     }
     const void *fn = map_fn_any(storage, vpt, guard);
     if (!fn)

@@ -1,0 +1,79 @@
+// nsli_sumsq.cuh -- ||a_i||^2 of stored rows with little binary64 work.
+//
+// GB300 executes binary64 at a small fraction of its binary32 rate, and a
+// plain binary64 sum of squares (one conversion and one binary64 FMA per
+// entry) bounds the set-up and row-update kernels.  Every stored value of a
+// binary32 / bf16 / FP8 row is a binary32 number, so each thread instead
+// keeps an unevaluated pair s + c of binary32 numbers ("double-float"):
+//   v^2 = p + e exactly (p = fl(v v), e = fma(v, v, -p)),
+//   s + p = t + err exactly (two-sum),
+//   c += err + e, then (s, c) = fast-two-sum(t, c), so |c| <= ulp(s) / 2.
+// Every 8 entries the pair is added to a binary64 accumulator (two binary64
+// additions for 8 entries instead of 16 operations).  The pair carries about
+// 48 significant bits, so each group of 8 is summed to within a few units of
+// 2^-48 relative and the result agrees with a binary64 sum to about 1e-14.
+// Values whose square could leave the binary32 normal range (|v| outside
+// [2^-60, 2^60]) are squared and added in binary64 directly.  The order is
+// fixed per thread, so the set-up kernel and the row-update kernel, which
+// both use this, give identical norms for identical rows.  Every operation is
+// an explicit round-to-nearest intrinsic so no multiply-add is contracted.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nsli {
+
+struct SumSq {
+    double acc;
+    float s, c;
+    int k;
+};
+
+__device__ __forceinline__ SumSq sumsq_init()
+{
+    SumSq q;
+    q.acc = 0.0;
+    q.s = 0.0f;
+    q.c = 0.0f;
+    q.k = 0;
+    return q;
+}
+
+__device__ __forceinline__ void sumsq_flush(SumSq &q)
+{
+    q.acc = __dadd_rn(q.acc, (double)q.s);
+    q.acc = __dadd_rn(q.acc, (double)q.c);
+    q.s = 0.0f;
+    q.c = 0.0f;
+    q.k = 0;
+}
+
+__device__ __forceinline__ void sumsq_add(SumSq &q, float v)
+{
+    const float a = fabsf(v);
+    if (a == 0.0f)
+        return;
+    if (a < 0x1p-60f || a > 0x1p60f) {
+        q.acc = __fma_rn((double)v, (double)v, q.acc);
+        return;
+    }
+    const float p = __fmul_rn(v, v);
+    const float e = __fmaf_rn(v, v, -p);          // p + e = v^2 exactly
+    const float t = __fadd_rn(q.s, p);            // two-sum: s + p = t + err
+    const float bp = __fsub_rn(t, q.s);
+    const float err = __fadd_rn(__fsub_rn(q.s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    const float c = __fadd_rn(q.c, __fadd_rn(err, e));
+    const float s2 = __fadd_rn(t, c);             // fast-two-sum (|t| >= |c|)
+    q.c = __fsub_rn(c, __fsub_rn(s2, t));
+    q.s = s2;
+    if (++q.k == 8)
+        sumsq_flush(q);
+}
+
+__device__ __forceinline__ double sumsq_value(SumSq &q)
+{
+    sumsq_flush(q);
+    return q.acc;
+}
+
+}  // namespace nsli

@@ -18,6 +18,7 @@
 
 #include "nsli.h"
 #include "nsli_internal.h"
+#include "nsli_sumsq.cuh"
 
 namespace nsli {
 namespace {
@@ -58,6 +59,39 @@ template <int S> __device__ __forceinline__ double stored_value(const void *src,
         const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
         const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
         return (double)__half2float(__half(hr)) * (double)scale;
+    }
+}
+
+// The stored value of a binary32 / bf16 / FP8 row as the binary32 number it
+// is (no binary64 conversion).
+template <int S> __device__ __forceinline__ float stored_value_f(const void *src, bool f64src, long long j,
+                                                                 float inv_scale, float scale, bool *bad)
+{
+    if (S == NSLI_F32) {
+        float v;
+        if (f64src) {
+            const double d = static_cast<const double *>(src)[j];
+            if (!isfinite(d))
+                *bad = true;
+            v = __double2float_rn(d);
+        } else {
+            v = static_cast<const float *>(src)[j];
+            if (!isfinite(v))
+                *bad = true;
+        }
+        return v;
+    } else if (S == NSLI_BF16) {
+        const float a = static_cast<const float *>(src)[j];
+        if (!isfinite(a))
+            *bad = true;
+        return __bfloat162float(__float2bfloat16_rn(a));
+    } else {
+        const float a = static_cast<const float *>(src)[j];
+        if (!isfinite(a))
+            *bad = true;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        return __fmul_rn(__half2float(__half(hr)), scale);   // exact: scale is a power of two
     }
 }
 
@@ -134,20 +168,38 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
         inv_scale = ldexpf(1.0f, -e);
     }
 
-    // pass 1: norm of the stored values (same order as the set-up kernel:
-    // thread t adds j = t, t + 256, ... in turn); kUnroll loads in flight
+    // pass 1: norm of the stored values (same order and arithmetic as the
+    // set-up kernel: thread t adds j = t, t + 256, ... in turn; binary64 for
+    // binary64 storage, else the double-float sum of nsli_sumsq.cuh);
+    // kUnroll loads in flight
     double n2 = 0.0;
+    SumSq sq = sumsq_init();
     for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
-        double v[kUnroll];
+        if constexpr (S == NSLI_F64) {
+            double v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const long long j = j0 + (long long)u * kThreads;
-            v[u] = j < p.n ? stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0;
+            for (int u = 0; u < kUnroll; ++u) {
+                const long long j = j0 + (long long)u * kThreads;
+                v[u] = j < p.n ? stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                n2 += v[u] * v[u];
+        } else {
+            float v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const long long j = j0 + (long long)u * kThreads;
+                v[u] = j < p.n ? stored_value_f<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (isfinite(v[u]))
+                    sumsq_add(sq, v[u]);
         }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            n2 += v[u] * v[u];
     }
+    if (S != NSLI_F64)
+        n2 = sumsq_value(sq);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
         n2 += __shfl_xor_sync(0xffffffffu, n2, off);

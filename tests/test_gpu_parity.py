@@ -379,8 +379,22 @@ def test_full_size_131072x16384_quantized_one_step(cfg3_system, storage):
 
 # ------------------------------------------------------------------ long rows
 
+# four rows per group (the default L2 budget) for all but the last two (two
+# and one rows); partial sums in shared memory except fp8 70000 and the
+# binary32 rows of 60000 columns and more
 LONG = [("f32", 600, 20000), ("bf16", 300, 40000), ("fp8", 200, 70000), ("f64", 200, 9000),
-        ("f32", 153, 16388)]
+        ("f32", 153, 16388), ("f32", 400, 60000), ("bf16", 40, 40000), ("f32", 200, 54000),
+        ("f32", 200, 70000), ("f32", 160, 140000)]
+
+
+@pytest.mark.parametrize("budget_mb", ["8", "30", "512"])
+@pytest.mark.parametrize("storage,m,n", [("f32", 600, 20000), ("bf16", 300, 40000)])
+def test_long_rows_every_group_size(monkeypatch, budget_mb, storage, m, n):
+    """The L2 budget for the rows of a group (NSLI_LONG_L2_MB) picks one,
+    two or four rows per group; all give the oracle's step, with the
+    partial sums in shared memory."""
+    monkeypatch.setenv("NSLI_LONG_L2_MB", budget_mb)
+    test_long_rows_one_step_and_trajectory(storage, m, n)
 
 
 @pytest.mark.parametrize("storage,m,n", LONG)
