@@ -412,7 +412,7 @@ def time_serving(nsli, torch, seconds):
             break
     elapsed = clock() - t0
     done = srv.done
-    lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
+    lat = np.array([r.latency for r in done])
     feas = [r for r in done if r.status == nsli.OK]
     iters = srv.problem_iterations
     out = {"requests": len(arrivals), "arrival_rate_per_s": cfg["rate"], "stream_s": seconds,
@@ -420,8 +420,8 @@ def time_serving(nsli, torch, seconds):
            "left_queued": len(srv.queue), "left_running": len(srv.live),
            "iteration_budget": cfg["max_iter"], "elapsed_s": elapsed,
            "solves_per_s": len(done) / elapsed, "problem_iterations_per_s": iters / elapsed,
-           "p50_time_to_result_ms": float(np.percentile(lat, 50) * 1e3),
-           "p99_time_to_result_ms": float(np.percentile(lat, 99) * 1e3),
+           "p50_time_to_result_ms": float(np.percentile(lat, 50) * 1e3) if done else None,
+           "p99_time_to_result_ms": float(np.percentile(lat, 99) * 1e3) if done else None,
            "p50_time_to_feasible_ms": float(np.percentile([r.latency for r in feas], 50) * 1e3) if feas else None,
            "p99_time_to_feasible_ms": float(np.percentile([r.latency for r in feas], 99) * 1e3) if feas else None,
            "grouped_round_gbs": srv.bytes_streamed / max(srv.busy_s, 1e-9) / 1e9,
@@ -464,7 +464,7 @@ def run_reference(args):
             "cpu_baseline": dict(vals[-1], value=rate),
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": el}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, allow_nan=False), flush=True)
     return 0
 
 
@@ -633,7 +633,7 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, allow_nan=False), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
