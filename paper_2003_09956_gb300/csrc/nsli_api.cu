@@ -34,6 +34,12 @@ struct nsli_solver {
     void *A = nullptr, *meta = nullptr, *x = nullptr, *part_y = nullptr;
     double *b0_64 = nullptr, *av_64 = nullptr, *n2_64 = nullptr, *part_dx = nullptr, *ybuf = nullptr,
            *dtmp = nullptr, *x64 = nullptr;
+    // ||a_i||^2 behind the row records (binary32 / bf16 / fp8 storage: the
+    // quick double-float sum; otherwise the same array as n2_64), and whether
+    // the binary64 norms n2_64 are up to date (they are computed from the
+    // stored rows when the binary64 check or nsli_get_norms2 needs them)
+    double *n2_meta = nullptr;
+    bool n2_64_valid = true;
     float *scale = nullptr;
     PartStat *part_stat = nullptr;
     DevState *st = nullptr;
@@ -107,6 +113,7 @@ void free_all(nsli_solver *h)
     void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
                    h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags,
                    (h->x64 != h->x) ? (void *)h->x64 : nullptr,
+                   (h->n2_meta != h->n2_64) ? (void *)h->n2_meta : nullptr,
                    h->rp, h->cp, h->ci, h->ri, h->row_cnt, h->col_cnt, h->row_pieces, h->col_pieces,
                    h->va, h->vc, h->coef, h->row_slots, h->col_slots};
     for (void *p : dev)
@@ -327,9 +334,25 @@ double ord_dec(unsigned long long u)
     return d;
 }
 
+// The binary64 norms of the stored rows, if rows changed since they were
+// last taken (dense binary32 / bf16 / fp8 storage).
+int ensure_norms64(nsli_solver *h)
+{
+    if (h->n2_64_valid)
+        return NSLI_OK;
+    CK(stored_norms64_launch(h->storage, h->stream, h->A, h->scale, h->ld, h->n, h->m, h->n2_64),
+       "binary64 row norms");
+    h->launches += 1;
+    h->n2_64_valid = true;
+    return NSLI_OK;
+}
+
 // Binary64 check at the current x and tick; fills h->last_check fields.
 int run_verify(nsli_solver *h)
 {
+    int rc = ensure_norms64(h);
+    if (rc != NSLI_OK)
+        return rc;
     CK(cudaMemsetAsync(h->ver, 0, sizeof(VerOut), h->stream), "clear check");
     VerifyArgs a;
     a.A = h->A;
@@ -462,6 +485,10 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
     CKC(cudaMalloc((void **)&h->b0_64, (size_t)m * 8), "allocate b0");
     CKC(cudaMalloc((void **)&h->av_64, (size_t)m * 8), "allocate Av");
     CKC(cudaMalloc((void **)&h->n2_64, (size_t)m * 8), "allocate norms");
+    if (storage == NSLI_F64)
+        h->n2_meta = h->n2_64;
+    else
+        CKC(cudaMalloc((void **)&h->n2_meta, (size_t)m * 8), "allocate record norms");
     if (storage == NSLI_FP8E4M3)
         CKC(cudaMalloc((void **)&h->scale, (size_t)m * 4), "allocate row scales");
     CKC(cudaMalloc(&h->x, (size_t)h->ld * accb), "allocate x");
@@ -547,9 +574,10 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
         pa.row0 = r0;
         pa.rows = rows;
         pa.norms_in = norms_dev;
-        pa.n2_64 = h->n2_64;
+        pa.n2_64 = h->n2_meta;
         pa.scale = h->scale;
         pa.flags = h->flags;
+        pa.fast = 1;
         err = prep_launch(storage, s, pa);
         h->launches += 1;
         if (!a_on_device && err == cudaSuccess)
@@ -560,12 +588,20 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
         ma.meta = h->meta;
         ma.b0_64 = h->b0_64;
         ma.av_64 = h->av_64;
-        ma.n2_64 = h->n2_64;
+        ma.n2_64 = h->n2_meta;
         ma.scale = h->scale;
         ma.m = m;
         ma.flags = h->flags;
         err = meta_launch(storage == NSLI_F64, s, ma);
         h->launches += 1;
+    }
+    // binary64 norms: the same array for binary64 storage, the user's norms
+    // if given, else taken from the stored rows when first needed
+    if (err == cudaSuccess && h->n2_meta != h->n2_64) {
+        if (norms2)
+            err = cudaMemcpyAsync(h->n2_64, h->n2_meta, (size_t)m * 8, cudaMemcpyDeviceToDevice, s);
+        else
+            h->n2_64_valid = false;
     }
     if (err == cudaSuccess)
         err = cudaStreamSynchronize(s);
@@ -842,6 +878,7 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     CKC(cudaMemcpyAsync(h->dtmp, x0, (size_t)n * 8, cudaMemcpyDefault, s), "copy x0");
     CKC(x_from_f64_launch(storage == NSLI_F64, s, h->dtmp, h->x64, h->x, n, n, h->flags), "convert x0");
     const int ngrid = (int)std::max<long long>(1, std::min<long long>((long long)h->num_sms * 8, (m + 7) / 8));
+    h->n2_meta = h->n2_64;   // sparse rows: the binary64 norms serve the records too
     CKC(sparse_norms_launch(storage == NSLI_F64, ngrid, s, sp, h->n2_64, h->flags), "row norms");
     if (norms2)
         CKC(cudaMemcpyAsync(h->n2_64, norms2, (size_t)m * 8, cudaMemcpyDefault, s), "copy norms");
@@ -893,7 +930,7 @@ int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
         ma.meta = h->meta;
         ma.b0_64 = h->b0_64;
         ma.av_64 = h->av_64;
-        ma.n2_64 = h->n2_64;
+        ma.n2_64 = h->n2_meta;
         ma.scale = h->scale;
         ma.m = h->m;
         ma.flags = h->flags;
@@ -965,7 +1002,7 @@ int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype,
         ua.rows = cnt;
         ua.b0_64 = h->b0_64;
         ua.av_64 = h->av_64;
-        ua.n2_64 = h->n2_64;
+        ua.n2_64 = h->n2_meta;
         ua.scale = h->scale;
         ua.meta = h->meta;
         ua.flags = h->flags;
@@ -980,6 +1017,8 @@ int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype,
         cudaFree(stage);
     }
     CK(err, "update rows");
+    if (h->n2_meta != h->n2_64)
+        h->n2_64_valid = false;   // taken again from the stored rows when needed
     return read_flags(h);
 }
 
@@ -1249,6 +1288,9 @@ int nsli_get_norms2(nsli_handle h, double *out)
 {
     if (!h || !out)
         return NSLI_ERR_ARG;
+    int rc = ensure_norms64(h);
+    if (rc != NSLI_OK)
+        return rc;
     CK(cudaMemcpyAsync(out, h->n2_64, (size_t)h->m * 8, cudaMemcpyDefault, h->stream), "copy norms");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
     return NSLI_OK;
@@ -1330,7 +1372,7 @@ long long problem_bytes(int storage, long long m, long long n, int num_sms)
     const int eb = storage == NSLI_F64 ? 8 : storage == NSLI_F32 ? 4 : storage == NSLI_BF16 ? 2 : 1;
     const long long ld = n + 16;
     const long long G = std::min<long long>(num_sms, m);
-    return m * ld * eb + m * (32 + 3 * 8 + 4) + G * ld * 8 + ld * 40 + (1 << 16);
+    return m * ld * eb + m * (32 + 4 * 8 + 4) + G * ld * 8 + ld * 40 + (1 << 16);
 }
 
 int items_of(nsli_solver *h)

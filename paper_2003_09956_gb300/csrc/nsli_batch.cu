@@ -831,6 +831,7 @@ int nsli_batch_create(nsli_batch *out, int64_t m, int64_t n, int32_t nprob, cons
             pa.n2_64 = h->n2_64;
             pa.scale = nullptr;
             pa.flags = h->flags;
+            pa.fast = 0;   // the binary64 norms: the batched check uses them
             err = prep_launch(NSLI_BF16, s, pa);
             if (err == cudaSuccess)
                 err = cudaStreamSynchronize(s);

@@ -159,11 +159,17 @@ struct PrepArgs {
     long long ld, n;
     long long row0, rows;   // rows of this launch (global index row0)
     const double *norms_in; // optional user norms (global index)
-    double *n2_64;
+    double *n2_64;          // receives ||a_i||^2 (global index)
     float *scale;           // FP8 row scale (global index) or NULL
     int *flags;
+    int fast;               // 1: the quick norm for the row records (no binary64
+                            // work per entry); 0: the binary64-accurate norm
 };
 cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a);
+// binary64-accurate ||a_i||^2 of the STORED rows (same value the set-up
+// kernel gives with fast = 0), for the binary64 check (nsli_update.cu)
+cudaError_t stored_norms64_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
+                                  long long n, long long m, double *n2_64);
 
 // rows row0 .. row0 + rows - 1 replaced from src (device, pitch lda, binary32
 // or binary64); b0_new (device, rows values) or NULL keeps b0 (nsli_update.cu)
@@ -177,7 +183,7 @@ struct UpdateArgs {
     const double *b0_new;
     double *b0_64;
     const double *av_64;
-    double *n2_64;
+    double *n2_64;       // receives the quick norm of each updated row (row records)
     float *scale;
     void *meta;
     int *flags;

@@ -1099,8 +1099,9 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
     }
 
     // ||a_i||^2 of the stored values: binary64 for binary64 storage, else the
-    // double-float accumulation of nsli_sumsq.cuh (same order as the
-    // row-update kernel)
+    // double-float accumulation of nsli_sumsq.cuh, folded into binary64 every
+    // 8 entries (fast = 0: the binary64 norms) or only at the end (fast = 1:
+    // the norm behind the row records, as in the row-update kernel)
     double n2 = 0.0;
     SumSq sq = sumsq_init();
     for (long long j = threadIdx.x; j < p.ld; j += blockDim.x) {
@@ -1117,7 +1118,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
                 bad = 1;
             static_cast<float *>(p.A)[gi * p.ld + j] = v;
             if (in && isfinite(v))
-                sumsq_add(sq, v);
+                p.fast ? sumsq_add<0>(sq, v) : sumsq_add<8>(sq, v);
         } else if (S == NSLI_BF16) {
             const float a = in ? s32[j] : 0.0f;
             if (in && !isfinite(a))
@@ -1126,7 +1127,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
             static_cast<__nv_bfloat16 *>(p.A)[gi * p.ld + j] = q;
             const float v = __bfloat162float(q);
             if (in && isfinite(v))
-                sumsq_add(sq, v);
+                p.fast ? sumsq_add<0>(sq, v) : sumsq_add<8>(sq, v);
         } else {
             const float a = in ? s32[j] : 0.0f;
             const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(a * inv_scale, __NV_SATFINITE, __NV_E4M3);
@@ -1134,7 +1135,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
             const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
             const float v = __fmul_rn(__half2float(__half(hr)), scale);   // exact: scale is a power of two
             if (in)
-                sumsq_add(sq, v);
+                p.fast ? sumsq_add<0>(sq, v) : sumsq_add<8>(sq, v);
         }
     }
     if (S != NSLI_F64)

@@ -12,6 +12,8 @@
 // additions for 8 entries instead of 16 operations).  The pair carries about
 // 48 significant bits, so each group of 8 is summed to within a few units of
 // 2^-48 relative and the result agrees with a binary64 sum to about 1e-14.
+// Without the periodic fold (FOLD = 0) the pair carries the whole per-thread
+// sum and only the final value is converted: no binary64 work per entry.
 // Values whose square could leave the binary32 normal range (|v| outside
 // [2^-60, 2^60]) are squared and added in binary64 directly.  The order is
 // fixed per thread, so the set-up kernel and the row-update kernel, which
@@ -48,7 +50,11 @@ __device__ __forceinline__ void sumsq_flush(SumSq &q)
     q.k = 0;
 }
 
-__device__ __forceinline__ void sumsq_add(SumSq &q, float v)
+// FOLD = 8: fold into binary64 every 8 entries (accurate to ~1e-14: the
+// binary64 norms); FOLD = 0: never until the end (no binary64 work per
+// entry; accurate to ~1e-12 for a few hundred entries per thread, which is
+// ample for the binary32 row records).
+template <int FOLD = 8> __device__ __forceinline__ void sumsq_add(SumSq &q, float v)
 {
     const float a = fabsf(v);
     if (a == 0.0f)
@@ -66,7 +72,7 @@ __device__ __forceinline__ void sumsq_add(SumSq &q, float v)
     const float s2 = __fadd_rn(t, c);             // fast-two-sum (|t| >= |c|)
     q.c = __fsub_rn(c, __fsub_rn(s2, t));
     q.s = s2;
-    if (++q.k == 8)
+    if (FOLD > 0 && ++q.k == FOLD)
         sumsq_flush(q);
 }
 

@@ -169,9 +169,9 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     }
 
     // pass 1: norm of the stored values (same order and arithmetic as the
-    // set-up kernel: thread t adds j = t, t + 256, ... in turn; binary64 for
-    // binary64 storage, else the double-float sum of nsli_sumsq.cuh);
-    // kUnroll loads in flight
+    // set-up kernel's quick norm: thread t adds j = t, t + 256, ... in turn;
+    // binary64 for binary64 storage, else the double-float sum of
+    // nsli_sumsq.cuh folded only at the end); kUnroll loads in flight
     double n2 = 0.0;
     SumSq sq = sumsq_init();
     for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
@@ -195,7 +195,7 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
                 if (isfinite(v[u]))
-                    sumsq_add(sq, v[u]);
+                    sumsq_add<0>(sq, v[u]);
         }
     }
     if (S != NSLI_F64)
@@ -253,7 +253,70 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     }
 }
 
+// Binary64-accurate ||a_i||^2 of stored rows, one block per row: the
+// set-up kernel's order and arithmetic with fast = 0 (thread t adds
+// j = t, t + 256, ...; double-float pairs folded into binary64 every 8
+// entries; the fixed block sum), from the stored values.
+template <int S>
+__global__ void __launch_bounds__(kThreads) stored_norms64_kernel(const void *A, const float *scale, long long ld,
+                                                                  long long n, long long m, double *n2_64)
+{
+    const long long i = blockIdx.x;
+    if (i >= m)
+        return;
+    __shared__ double sred[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double n2 = 0.0;
+    SumSq sq = sumsq_init();
+    for (long long j = threadIdx.x; j < n; j += kThreads) {
+        if constexpr (S == NSLI_F64) {
+            const double v = static_cast<const double *>(A)[i * ld + j];
+            n2 += v * v;
+        } else if constexpr (S == NSLI_F32) {
+            sumsq_add<8>(sq, static_cast<const float *>(A)[i * ld + j]);
+        } else if constexpr (S == NSLI_BF16) {
+            sumsq_add<8>(sq, __bfloat162float(static_cast<const __nv_bfloat16 *>(A)[i * ld + j]));
+        } else {
+            const __nv_fp8_storage_t q = static_cast<const unsigned char *>(A)[i * ld + j];
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+            sumsq_add<8>(sq, __fmul_rn(__half2float(__half(hr)), scale[i]));
+        }
+    }
+    if (S != NSLI_F64)
+        n2 = sumsq_value(sq);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+    if (lane == 0)
+        sred[wid] = n2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q)
+            t += sred[q];
+        n2_64[i] = t;
+    }
+}
+
 }  // namespace
+
+cudaError_t stored_norms64_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
+                                  long long n, long long m, double *n2_64)
+{
+    if (m <= 0)
+        return cudaSuccess;
+    const unsigned grid = (unsigned)m;
+    switch (storage) {
+    case NSLI_F64: stored_norms64_kernel<NSLI_F64><<<grid, kThreads, 0, s>>>(A, scale, ld, n, m, n2_64); break;
+    case NSLI_F32: stored_norms64_kernel<NSLI_F32><<<grid, kThreads, 0, s>>>(A, scale, ld, n, m, n2_64); break;
+    case NSLI_BF16: stored_norms64_kernel<NSLI_BF16><<<grid, kThreads, 0, s>>>(A, scale, ld, n, m, n2_64); break;
+    case NSLI_FP8E4M3:
+        stored_norms64_kernel<NSLI_FP8E4M3><<<grid, kThreads, 0, s>>>(A, scale, ld, n, m, n2_64);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t update_rows_launch(int storage, cudaStream_t s, const UpdateArgs &a)
 {
