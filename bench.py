@@ -115,9 +115,16 @@ def step_bytes(m, n, storage):
     return map_bytes(m, n, storage) + 4 * n
 
 
+MAP_SOURCE_END = "// --------------------------------------------------- Map, long rows --------"
+
+
 def kernels_sha():
-    src = os.path.join(ROOT, "paper_2003_09956_gb300", "csrc", "nsli_kernels.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    """Hash of the source the Map kernel is compiled from: nsli_kernels.cu up
+    to the long-row section (helpers, the Map body and its kernels; the
+    kernels after it do not enter the Map)."""
+    src = open(os.path.join(ROOT, "paper_2003_09956_gb300", "csrc", "nsli_kernels.cu")).read()
+    end = src.find(MAP_SOURCE_END)
+    return hashlib.sha256(src[:end if end >= 0 else len(src)].encode()).hexdigest()[:12]
 
 
 def profiled_traffic(workload, storage):
