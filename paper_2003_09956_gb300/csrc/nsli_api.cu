@@ -12,10 +12,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nsli.h"
 #include "nsli_internal.h"
 
 using namespace nsli;
+
+namespace {
+// An NVTX range around each ABI call, named after it, so a profiler's
+// timeline shows which call issued which kernels (free without a profiler).
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+}  // namespace
 
 struct nsli_solver {
     int device = 0;
@@ -435,6 +448,7 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
                 int64_t lda, const double *b0, const double *norms2, const double *Av, const double *x0,
                 void *stream)
 {
+    Trace trace_("nsli_create");
     if (!out)
         return NSLI_ERR_ARG;
     *out = nullptr;
@@ -623,6 +637,7 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
                     const int32_t *col_idx, const double *val, const double *b0, const double *norms2,
                     const double *Av, const double *x0, void *stream)
 {
+    Trace trace_("nsli_create_csr");
     if (!out)
         return NSLI_ERR_ARG;
     *out = nullptr;
@@ -921,6 +936,7 @@ int nsli_sync(nsli_handle h)
 
 int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
 {
+    Trace trace_("nsli_update_b");
     if (!h)
         return NSLI_ERR_ARG;
     if (b0) {
@@ -949,6 +965,7 @@ int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
 int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype, const void *A, int64_t lda,
                      const double *b0)
 {
+    Trace trace_("nsli_update_rows");
     if (!h)
         return NSLI_ERR_ARG;
     if (h->sparse)
@@ -1024,6 +1041,7 @@ int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype,
 
 int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)
 {
+    Trace trace_("nsli_iterate");
     if (!h)
         return NSLI_ERR_ARG;
     int rc = validate_params(h, p);
@@ -1054,6 +1072,7 @@ int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)
 
 int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter, double *kernel_ms)
 {
+    Trace trace_("nsli_iterate_timed");
     if (!h || !kernel_ms)
         return NSLI_ERR_ARG;
     int rc = validate_params(h, p);
@@ -1111,6 +1130,7 @@ int nsli_iterate_timed(nsli_handle h, const nsli_params *p, int64_t n_iter, doub
 
 int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
 {
+    Trace trace_("nsli_solve");
     if (!h)
         return NSLI_ERR_ARG;
     int rc = validate_params(h, p);
@@ -1174,6 +1194,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
 
 int nsli_residual_max(nsli_handle h, double *max_viol, double *max_viol_norm)
 {
+    Trace trace_("nsli_residual_max");
     if (!h)
         return NSLI_ERR_ARG;
     int rc = run_verify(h);
@@ -1188,6 +1209,7 @@ int nsli_residual_max(nsli_handle h, double *max_viol, double *max_viol_norm)
 
 int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats)
 {
+    Trace trace_("nsli_map_reduce");
     if (!h)
         return NSLI_ERR_ARG;
     if (h->sparse) {
@@ -1221,6 +1243,7 @@ int nsli_map_reduce(nsli_handle h, double *y, int64_t *violated, double *stats)
 
 int nsli_get_x(nsli_handle h, double *x)
 {
+    Trace trace_("nsli_get_x");
     if (!h || !x)
         return NSLI_ERR_ARG;
     CK(cudaMemcpyAsync(x, h->x64, (size_t)h->n * 8, cudaMemcpyDefault, h->stream), "copy x");
@@ -1230,6 +1253,7 @@ int nsli_get_x(nsli_handle h, double *x)
 
 int nsli_set_x(nsli_handle h, const double *x)
 {
+    Trace trace_("nsli_set_x");
     if (!h || !x)
         return NSLI_ERR_ARG;
     CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream), "clear flags");
@@ -1515,6 +1539,7 @@ void nsli_pool_destroy(nsli_pool p)
 int nsli_pool_add(nsli_pool p, int64_t m, int64_t n, const float *A, int64_t lda, const double *b0,
                   const double *Av, const double *x0, const nsli_params *prm, int64_t *slot)
 {
+    Trace trace_("nsli_pool_add");
     if (!p || !slot || !prm)
         return NSLI_ERR_ARG;
     if (m < 1 || n < 1 || lda < n || !A || !b0 || !x0)
@@ -1580,6 +1605,7 @@ int nsli_pool_remove(nsli_pool p, int64_t slot)
 
 int nsli_pool_step(nsli_pool p, int32_t rounds)
 {
+    Trace trace_("nsli_pool_step");
     if (!p || rounds < 0)
         return NSLI_ERR_ARG;
     if (p->dirty) {
@@ -1627,6 +1653,7 @@ int nsli_pool_set_ticks(nsli_pool p, const int64_t *slots, const int64_t *ticks,
 
 int nsli_pool_poll(nsli_pool p, int64_t *slots, int32_t *status, int64_t *iters, int64_t cap, int64_t *count)
 {
+    Trace trace_("nsli_pool_poll");
     if (!p || !count || cap < 0 || (cap > 0 && (!slots || !status || !iters)))
         return NSLI_ERR_ARG;
     *count = 0;
