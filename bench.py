@@ -6,9 +6,14 @@ b(k) = b0 + k rho Av, the fused Map over all m rows (residuals, positive
 slices, per-CTA sums), the deterministic Reduce, the stopping test and the
 step x <- x - lambda y / h.  Default workload: the dense random system
 m = 131072, n = 16384 (a_ij ~ N(0, 1), rho = 1e-4 per tick), A stored in
-binary32 (8 GiB, far larger than L2, so no flush is needed between steps);
-the bfloat16 and FP8-E4M3 storage of the same system are measured in the
-same run and reported under "variants".
+binary32 (8 GiB, far larger than L2, so no flush is needed between steps).
+Measured in the same run and reported under "variants": the bfloat16 and
+FP8-E4M3 storage of the same system, the model system's solve latency, a
+sparse system (4194304 x 1048576, 32 non-zeros per row), the same dense
+system with all of A rewritten before every iteration, the batched
+tensor-core form (64 problems sharing one A) and a serving stream.
+`--workload dense-108001x54000` measures the long-row Map at the paper's
+n = 54000.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nsli|reference]
 
