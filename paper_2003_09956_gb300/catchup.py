@@ -174,6 +174,16 @@ class GpuTrials:
         self.last = r
         return r["status"] == nsli.OK
 
+    def timed(self, rho: float):
+        """One solve from x0 at tick 0, synchronised: (reached, iterations,
+        seconds), the seconds including the host's polls and the binary64
+        confirmation of the stop (the running time of a solve)."""
+        self.solver.sync()
+        t0 = time.perf_counter()
+        ok = self(rho)
+        self.solver.sync()
+        return ok, int(self.last["iters"]), time.perf_counter() - t0
+
     def iteration_rate(self, rho: float, min_seconds: float = 0.3) -> float:
         """Iterations per second of the same rule at the same rate, timed
         over a fixed iteration count (no stopping test)."""
@@ -192,8 +202,26 @@ class GpuTrials:
             k *= 2
 
 
+CURVE_FRACTIONS = (0.0, 0.25, 0.5, 0.75, 0.9, 0.97, 1.0)
+
+
+def time_vs_rate(timed, rho_max: float, fractions=CURVE_FRACTIONS, repeats: int = 3) -> list:
+    """Running time of a solve against the displacement rate (the kind of
+    curve Section 5 reports): for rho = f rho_max, the median over `repeats`
+    solves of timed(rho) -> (reached, iterations, seconds)."""
+    out = []
+    for f in fractions:
+        rho = f * rho_max
+        runs = [timed(rho) for _ in range(repeats)]
+        secs = sorted(r[2] for r in runs)
+        out.append({"fraction_of_rho_max": f, "rho_per_iteration": rho,
+                    "reached": all(r[0] for r in runs), "iterations": runs[0][1],
+                    "solve_ms": 1e3 * secs[len(secs) // 2]})
+    return out
+
+
 def catchup(p: dict, rule: str, lam: float, eps: float = 1e-7, max_iter: int = 20000,
-            storage: str = "f64", rho0: float | None = None, steps: int = 12) -> dict:
+            storage: str = "f64", rho0: float | None = None, steps: int = 12, curve: bool = False) -> dict:
     """Catch-up rate of one rule on one system, with the units conversion."""
     out = {"system": p.get("name", ""), "m": int(p["m"]), "n": int(p["n"]), "rule": rule,
            "lambda": lam, "eps": eps, "max_iter": max_iter, "storage": storage}
@@ -219,6 +247,11 @@ def catchup(p: dict, rule: str, lam: float, eps: float = 1e-7, max_iter: int = 2
             # (the paper's "coordinate-wise displacement") and as a vector
             out["units_per_s_per_coordinate"] = lo * ips
             out["units_per_s_total"] = lo * ips * p["v_norm"]
+            if curve:
+                pts = time_vs_rate(t.timed, lo)
+                for q in pts:
+                    q["units_per_s_per_coordinate"] = q["rho_per_iteration"] * ips
+                out["time_vs_rate"] = pts
     return out
 
 
@@ -237,6 +270,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--curve", action="store_true",
+                    help="also time solves at fractions of the catch-up rate (time against rate)")
     args = ap.parse_args()
     nsli.load()
     systems = []
@@ -266,7 +301,7 @@ def main():
             runs.append(("modap", c * math.sqrt(p["n"])))
         for rule, lam in runs:
             r = catchup(p, rule, lam, eps=args.eps, max_iter=args.max_iter, storage=storage,
-                        steps=args.steps)
+                        steps=args.steps, curve=args.curve)
             print(json.dumps(r), flush=True)
         p.pop("A", None)
 

@@ -94,3 +94,21 @@ def test_sparse_model_system_translation_matches_dense():
     np.testing.assert_array_equal(workloads.csr_to_dense(p["rp"], p["ci"], p["val"], 6), q["A"])
     np.testing.assert_array_equal(p["Av"], q["Av"])
     np.testing.assert_array_equal(p["x0"], q["x0"])
+
+
+def test_time_vs_rate_curve_host_logic():
+    """The curve takes the median of the repeats at each fraction of the
+    catch-up rate and reports whether every repeat reached the polytope."""
+    calls = []
+
+    def timed(rho):
+        calls.append(rho)
+        k = len(calls)
+        return rho < 0.95, 10 + int(100 * rho), [0.3, 0.1, 0.2][k % 3]
+
+    pts = catchup.time_vs_rate(timed, 1.0, fractions=(0.0, 0.5, 1.0), repeats=3)
+    assert [q["fraction_of_rho_max"] for q in pts] == [0.0, 0.5, 1.0]
+    assert calls == [0.0] * 3 + [0.5] * 3 + [1.0] * 3
+    assert all(q["solve_ms"] == pytest.approx(200.0) for q in pts)
+    assert [q["reached"] for q in pts] == [True, True, False]
+    assert pts[1]["iterations"] == 60
