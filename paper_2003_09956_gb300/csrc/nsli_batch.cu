@@ -21,7 +21,7 @@
 // the three partial dots of each problem.
 //
 // Kernel layout: 6 warps.  Warp 0 issues the TMA tile loads (128B swizzle)
-// into a 4-stage shared-memory ring; warp 1 allocates 512 TMEM columns (two
+// into a 5-stage shared-memory ring; warp 1 allocates 512 TMEM columns (two
 // 128 x 256 binary32 accumulators) and one of its threads issues
 // tcgen05.mma; warps 2-5 drain an accumulator with tcgen05.ld while the
 // other one is being filled.  Every wait is bounded.
@@ -43,7 +43,13 @@ namespace batch {
 
 constexpr int BM = 128;        // rows of the A operand per tile (TMEM lanes)
 constexpr int BK = 64;         // K per stage: 64 bf16 = one 128-byte swizzle row
-constexpr int NSTAGE = 4;
+#ifndef NSLI_BATCH_STAGES
+#define NSLI_BATCH_STAGES 5
+#endif
+constexpr int NSTAGE = NSLI_BATCH_STAGES;   // shared-memory ring depth (5 x 40 KB fits in 227 KB)
+// mbarrier slots after the ring: full[s], empty[s], accumulator full[2], accumulator empty[2]
+constexpr int kBarFull = 0, kBarEmpty = NSTAGE, kBarTFull = 2 * NSTAGE, kBarTEmpty = 2 * NSTAGE + 2;
+constexpr int kBarCount = 2 * NSTAGE + 4;
 constexpr int kThreads = 192;  // 6 warps
 constexpr int kAccCols = 256;  // TMEM columns per accumulator
 constexpr int kTmemCols = 512;
@@ -52,6 +58,7 @@ constexpr int kStageA = BM * BK * 2;          // 16 KB
 constexpr int kStageB = kMaxBN * BK * 2;      // 24 KB
 constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kSmemBytes = 1024 + NSTAGE * kStageBytes + 256;
+static_assert(kBarCount * 8 + 16 <= 256, "barriers fit behind the ring");
 constexpr long long kWaitCycles = 4000000000ll;
 
 struct State {
@@ -215,9 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned int base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(sbase + NSTAGE * kStageBytes);
-    // full[0..3], empty[4..7], tfull[8..9], tempty[10..11]
-    unsigned int *tmem_holder = reinterpret_cast<unsigned int *>(bars + 12);
-    volatile int *abort = reinterpret_cast<volatile int *>(bars + 13);
+    unsigned int *tmem_holder = reinterpret_cast<unsigned int *>(bars + kBarCount);
+    volatile int *abort = reinterpret_cast<volatile int *>(bars + kBarCount + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int BN = e.BN;
@@ -226,12 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[4 + s]), 1);
+            mbar_init(smem_u32(&bars[kBarFull + s]), 1);
+            mbar_init(smem_u32(&bars[kBarEmpty + s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
-            mbar_init(smem_u32(&bars[8 + a]), 1);
-            mbar_init(smem_u32(&bars[10 + a]), 4);
+            mbar_init(smem_u32(&bars[kBarTFull + a]), 1);
+            mbar_init(smem_u32(&bars[kBarTEmpty + a]), 4);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -259,11 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int kbeg = ks * e.ktiles;
                 const int kend = min(kbeg + e.ktiles, e.ktiles_total);
                 for (int kc = kbeg; kc < kend; ++kc) {
-                    if (!wait_bar(smem_u32(&bars[4 + s]), ph ^ 1u, abort)) {
+                    if (!wait_bar(smem_u32(&bars[kBarEmpty + s]), ph ^ 1u, abort)) {
                         ok = false;
                         break;
                     }
-                    const unsigned int fb = smem_u32(&bars[s]);
+                    const unsigned int fb = smem_u32(&bars[kBarFull + s]);
                     mbar_expect_tx(fb, stage_tx);
                     const unsigned int sa = base + s * kStageBytes;
                     tma_load_2d(sa, &tmA, kc * BK, tile * BM, fb);
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // wait (bounded) until the MMA side has consumed every issued stage
             if (ok) {
                 for (int q = 0; q < NSTAGE; ++q) {
-                    if (!wait_bar(smem_u32(&bars[4 + s]), ph ^ 1u, abort))
+                    if (!wait_bar(smem_u32(&bars[kBarEmpty + s]), ph ^ 1u, abort))
                         break;
                     if (++s == NSTAGE) {
                         s = 0;
@@ -298,12 +304,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ks = w / e.mtiles;
                 const int kbeg = ks * e.ktiles;
                 const int kend = min(kbeg + e.ktiles, e.ktiles_total);
-                if (!wait_bar(smem_u32(&bars[10 + acc]), aph ^ 1u, abort))
+                if (!wait_bar(smem_u32(&bars[kBarTEmpty + acc]), aph ^ 1u, abort))
                     break;
                 tc_fence_after();
                 const unsigned int dcol = tmem_base + (unsigned int)(acc * kAccCols);
                 for (int kc = kbeg; kc < kend; ++kc) {
-                    if (!wait_bar(smem_u32(&bars[s]), ph, abort)) {
+                    if (!wait_bar(smem_u32(&bars[kBarFull + s]), ph, abort)) {
                         ok = false;
                         break;
                     }
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const unsigned long long bd = sdesc(sa + kStageA + k16 * 32);
                         mma_bf16(dcol, ad, bd, idesc, (kc > kbeg || k16 > 0) ? 1u : 0u);
                     }
-                    mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
+                    mma_commit(smem_u32(&bars[kBarEmpty + s]));  // frees the stage once these MMAs have read it
                     if (++s == NSTAGE) {
                         s = 0;
                         ph ^= 1u;
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok)
                     break;
-                mma_commit(smem_u32(&bars[8 + acc]));    // accumulator ready
+                mma_commit(smem_u32(&bars[kBarTFull + acc]));    // accumulator ready
                 if (++acc == 2) {
                     acc = 0;
                     aph ^= 1u;
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float rho = (float)e.st->rho;
         for (int w = blockIdx.x; w < e.nwork; w += gridDim.x) {
             const int tile = w % e.mtiles, ks = w / e.mtiles;
-            if (!wait_bar(smem_u32(&bars[8 + acc]), aph, abort))
+            if (!wait_bar(smem_u32(&bars[kBarTFull + acc]), aph, abort))
                 break;
             tc_fence_after();
             const long long row = (long long)tile * BM + 32 * lg + lane;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(smem_u32(&bars[10 + acc]));
+                mbar_arrive(smem_u32(&bars[kBarTEmpty + acc]));
             if (++acc == 2) {
                 acc = 0;
                 aph ^= 1u;
