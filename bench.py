@@ -8,7 +8,8 @@ step x <- x - lambda y / h.  Default workload: the dense random system
 m = 131072, n = 16384 (a_ij ~ N(0, 1), rho = 1e-4 per tick), A stored in
 binary32 (8 GiB, far larger than L2, so no flush is needed between steps).
 Measured in the same run and reported under "variants": the bfloat16 and
-FP8-E4M3 storage of the same system, the model system's solve latency, a
+FP8-E4M3 storage of the same system, the model system's solve latency
+(dense binary64 rows on the grid kernels, and compressed rows on one CTA), a
 sparse system (4194304 x 1048576, 32 non-zeros per row), the same dense
 system with all of A rewritten before every iteration, the batched
 tensor-core form (64 problems sharing one A) and a serving stream.
@@ -254,6 +255,37 @@ def time_model_system(nsli, seeds=30):
             "p50_solve_ms": float(np.percentile(t, 50)), "p99_solve_ms": float(np.percentile(t, 99)),
             "median_iterations": float(np.median(iters)),
             "us_per_iteration": float(np.median(t * 1e3 / np.array(iters))),
+            "max_rel_violation_f64": float(np.max(viol))}
+
+
+def time_model_system_csr(nsli, seeds=30):
+    """The same model systems held in compressed form (3n non-zeros), where
+    the whole solve runs on one CTA: blocks of up to 1024 iterations per
+    launch, state polls and the binary64 confirmation included."""
+    from paper_2003_09956_gb300 import workloads
+
+    times, iters, viol, launches = [], [], [], []
+    for sd in range(seeds):
+        p = workloads.model_system_csr(256, seed=sd)
+        with nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"],
+                               storage="f64") as s:
+            if sd == 0:
+                s.solve(stop="step", eps=1e-8, max_iter=100000)   # warm-up (module load)
+                s.set_x(p["x0"])
+            c0 = s.launch_count()
+            t0 = time.perf_counter()
+            r = s.solve(stop="step", eps=1e-8, max_iter=100000)
+            times.append(time.perf_counter() - t0)
+            launches.append(s.launch_count() - c0)
+            iters.append(r["iters"])
+            viol.append(r["max_viol"] / np.abs(p["b0"]).max())
+    t = np.array(times) * 1e3
+    return {"workload": "model system n=256 m=513 f64 in compressed rows (768 non-zeros), STEP 1e-8, "
+                        "one CTA per solve", "seeds": seeds,
+            "p50_solve_ms": float(np.percentile(t, 50)), "p99_solve_ms": float(np.percentile(t, 99)),
+            "median_iterations": float(np.median(iters)),
+            "us_per_iteration": float(np.median(t * 1e3 / np.array(iters))),
+            "launches_per_solve": float(np.median(launches)),
             "max_rel_violation_f64": float(np.max(viol))}
 
 
@@ -603,6 +635,7 @@ def main():
                         "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
 
     variants["model_system_f64"] = time_model_system(nsli)
+    variants["model_system_f64_csr"] = time_model_system_csr(nsli)
     if args.sparse:
         variants["sparse_f32"] = time_sparse(nsli, torch, args.sparse, K, W, peak)
     if args.matrix_updates:

@@ -71,6 +71,10 @@ struct nsli_solver {
     SegPiece *row_pieces = nullptr, *col_pieces = nullptr;
     void *va = nullptr, *vc = nullptr, *coef = nullptr, *row_slots = nullptr, *col_slots = nullptr;
     SparseArgs sp{};
+    // small systems: whole iteration blocks in one CTA (sparse_resident_kernel)
+    bool resident = false;
+    size_t res_smem = 0;
+    int *res_rows = nullptr, *res_cols = nullptr;
 
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
@@ -128,7 +132,7 @@ void free_all(nsli_solver *h)
                    (h->x64 != h->x) ? (void *)h->x64 : nullptr,
                    (h->n2_meta != h->n2_64) ? (void *)h->n2_meta : nullptr,
                    h->rp, h->cp, h->ci, h->ri, h->row_cnt, h->col_cnt, h->row_pieces, h->col_pieces,
-                   h->va, h->vc, h->coef, h->row_slots, h->col_slots};
+                   h->va, h->vc, h->coef, h->row_slots, h->col_slots, h->res_rows, h->res_cols};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -752,6 +756,29 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
         *nseg = hs;
         *nslots = slot;
     };
+    // One CTA runs whole blocks of iterations when its shared memory holds
+    // x64, y, x and c and the matrix (both orders) fits, with them, in the
+    // SM's 256 KB of L1 and shared memory: then an iteration reads nothing
+    // from L2.  NSLI_SPARSE_RESIDENT=0 never takes this path, =1 takes it
+    // whenever the shared memory suffices.
+    const size_t res_smem = sparse_resident_smem(storage == NSLI_F64, m, n);
+    const size_t res_total = res_smem + (size_t)nnz * 2 * (h->elem_bytes + 4) + (size_t)(m + n + 2) * 8;
+    {
+        const char *env = std::getenv("NSLI_SPARSE_RESIDENT");
+        const int force = env ? std::atoi(env) : -1;
+        h->resident = res_smem <= kResSmemMax && force != 0 && (force == 1 || res_total <= (200u << 10));
+        h->res_smem = res_smem;
+    }
+    std::vector<int> long_rows, long_cols;
+    if (h->resident) {
+        for (long long i = 0; i < m; ++i)
+            if (rp[i + 1] - rp[i] > kResLong)
+                long_rows.push_back((int)i);
+        for (long long j = 0; j < n; ++j)
+            if (cp[j + 1] - cp[j] > kResLong)
+                long_cols.push_back((int)j);
+    }
+
     SparseArgs &sp = h->sp;
     sp = SparseArgs{};
     sp.m = m;
@@ -878,6 +905,23 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     sp.st = h->st;
     sp.ignore_done = 0;
     sp.mode = 0;
+    if (h->resident) {
+        if (!long_rows.empty()) {
+            CKC(cudaMalloc((void **)&h->res_rows, long_rows.size() * 4), "allocate long row list");
+            CKC(cudaMemcpyAsync(h->res_rows, long_rows.data(), long_rows.size() * 4, cudaMemcpyHostToDevice, s),
+                "upload long row list");
+        }
+        if (!long_cols.empty()) {
+            CKC(cudaMalloc((void **)&h->res_cols, long_cols.size() * 4), "allocate long column list");
+            CKC(cudaMemcpyAsync(h->res_cols, long_cols.data(), long_cols.size() * 4, cudaMemcpyHostToDevice, s),
+                "upload long column list");
+        }
+        sp.res_long_rows = h->res_rows;
+        sp.res_long_cols = h->res_cols;
+        sp.n_res_long_rows = (int)long_rows.size();
+        sp.n_res_long_cols = (int)long_cols.size();
+        CKC(sparse_resident_prepare(storage == NSLI_F64, h->res_smem), "configure one-CTA kernel");
+    }
 
     CKC(cudaMemsetAsync(h->st, 0, sizeof(DevState), s), "clear state");
     CKC(cudaMemsetAsync(h->flags, 0, sizeof(int), s), "clear flags");
@@ -1051,6 +1095,16 @@ int nsli_iterate(nsli_handle h, const nsli_params *p, int64_t n_iter)
         return set_err(h, NSLI_ERR_ARG, "n_iter < 0");
     if ((rc = begin_run(h, p, NSLI_STOP_NONE, LLONG_MAX)) != NSLI_OK)
         return rc;
+    if (h->resident) {
+        const int B = p->block_iters > 0 ? p->block_iters : kResBlock;
+        for (long long done = 0; done < n_iter; done += B) {
+            CK(sparse_resident_launch(h->storage == NSLI_F64, h->stream, h->sp, h->res_smem,
+                                      (int)std::min<long long>(B, n_iter - done)),
+               "launch one-CTA iterations");
+            h->launches += 1;
+        }
+        return NSLI_OK;
+    }
     const int B = p->block_iters > 0 ? p->block_iters : 32;
     const long long full = n_iter / B;
     const long long rem = n_iter % B;
@@ -1138,8 +1192,8 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
         return rc;
     if ((rc = begin_run(h, p, p->stop, p->max_iter)) != NSLI_OK)
         return rc;
-    const int B = p->block_iters > 0 ? p->block_iters : 32;
-    if ((rc = ensure_graph(h, B, p->rule)) != NSLI_OK)
+    const int B = p->block_iters > 0 ? p->block_iters : (h->resident ? kResBlock : 32);
+    if (!h->resident && (rc = ensure_graph(h, B, p->rule)) != NSLI_OK)
         return rc;
     const int per = launches_per_iteration(h, p->rule);
     int status = NSLI_NOT_CONVERGED;
@@ -1148,8 +1202,14 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     const long long max_blocks = p->max_iter / B + p->max_iter + 4;
     bool finished = false;
     for (long long blk = 0; blk < max_blocks && !finished; ++blk) {
-        CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
-        h->launches += (long long)per * B;
+        if (h->resident) {
+            CK(sparse_resident_launch(h->storage == NSLI_F64, h->stream, h->sp, h->res_smem, B),
+               "launch one-CTA iterations");
+            h->launches += 1;
+        } else {
+            CK(cudaGraphLaunch(h->graph, h->stream), "launch iteration graph");
+            h->launches += (long long)per * B;
+        }
         if ((rc = read_state(h)) != NSLI_OK)
             return rc;
         const int sst = h->st_host->status;

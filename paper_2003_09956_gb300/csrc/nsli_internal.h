@@ -263,6 +263,10 @@ struct SparseArgs {
     int w_row, w_col;         // lanes per row / column (1, 2, 4, ..., 32)
     int ignore_done;          // run even when the done flag is set
     int mode;                 // 0: iteration; 1: Map and y only (no decision, no step)
+    // one-CTA runs of small systems (sparse_resident_kernel): the rows and
+    // columns with more than kResLong entries, taken by one warp each
+    const int *res_long_rows, *res_long_cols;
+    int n_res_long_rows, n_res_long_cols;
 };
 // resident CTAs per SM of the row / column kernel instances for these widths
 void sparse_blocks_per_sm(bool f64, int w_row, int w_col, int *row_bps, int *col_bps);
@@ -273,5 +277,15 @@ cudaError_t sparse_norms_launch(bool f64, int grid, cudaStream_t s, const Sparse
 cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const SparseArgs &a, const VerifyArgs &v);
 cudaError_t sparse_rows_launch(bool f64, cudaStream_t s, const SparseArgs &a, long long row0, long long rows,
                                double *out);
+
+// Small systems: a block of up to `iters` iterations (mode 0) in one launch
+// of one CTA whose shared memory holds x64, y, x and c.
+constexpr int kResThreads = 256;
+constexpr int kResLong = 32;             // longer rows / columns go to a warp each
+constexpr size_t kResSmemMax = 216 * 1024;
+constexpr int kResBlock = 1024;          // iterations per launch unless block_iters says otherwise
+size_t sparse_resident_smem(bool f64, long long m, long long n);
+cudaError_t sparse_resident_prepare(bool f64, size_t smem);
+cudaError_t sparse_resident_launch(bool f64, cudaStream_t s, const SparseArgs &a, size_t smem, int iters);
 
 }  // namespace nsli

@@ -520,6 +520,277 @@ template <typename T> __global__ void sparse_rows_kernel(const SparseArgs p, lon
         out[r * p.n + p.ci[e]] = (double)va[e];
 }
 
+// ---- small systems: a whole block of iterations in one CTA --------------------
+//
+// When the binary64 iterate, y, and x and the coefficients c in the
+// accumulation type fit in one CTA's shared memory, one CTA on one SM runs up
+// to `iters` iterations per launch: an iteration costs a few block barriers
+// instead of two or three launches and their grid-wide hand-offs.  The steps
+// and decisions are those of the grid kernels above, in an order of their
+// own: rows one per thread in CSR order (rows longer than kResLong by one
+// warp each: lane-strided partial sums, then a butterfly); the row counts and
+// maxima folded exactly (integers and order-preserving encodings); the stop
+// decision taken by every thread from the same totals; columns one per
+// thread in CSC order (long ones by warps), each giving the relaxed step of
+// its x_j, or ModAP's y_j followed by ||y|| and the step; the sum of dx^2 (of
+// y^2) folded in a fixed order.  Only x, x64 and DevState persist between
+// launches (global memory), so launches of any size give identical results.
+// The statistics a stop rule does not read are not formed: DevState keeps
+// h and max r_i always, max r_i / ||a_i|| only under EPSMEM and max |b_i|
+// only under MAXVIOL_REL (-inf / 0 otherwise).
+
+__device__ __forceinline__ double sp_ord_dec(unsigned long long u)
+{
+    const unsigned long long bits = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+// Fixed-order sum over the block (two barriers): every thread's value to
+// shared memory, warp 0 adds them lane-strided then by a butterfly.
+__device__ __forceinline__ double res_block_sum(double v, double *part, double *tot)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    part[tid] = v;
+    __syncthreads();
+    if (tid < 32) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kResThreads / 32; ++q)
+            t += part[lane + 32 * q];
+        t = warp_total(t);
+        if (lane == 0)
+            *tot = t;
+    }
+    __syncthreads();
+    return *tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const SparseArgs p, int iters)
+{
+    using Meta = typename SpTraits<T>::Meta;
+    DevState *st = p.st;
+    if (*(volatile int *)&st->done || iters <= 0)
+        return;
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    const long long n = p.n, m = p.m;
+    double *x64s = reinterpret_cast<double *>(res_smem);
+    double *ys = x64s + n;
+    T *xs = reinterpret_cast<T *>(ys + n);
+    T *cs = xs + n;
+    // row statistics of iteration k accumulate in slot k & 1
+    __shared__ unsigned long long sh_mv[2], sh_mn[2], sh_mb[2];
+    __shared__ int sh_h[2];
+    __shared__ double sh_part[kResThreads];
+    __shared__ double sh_tot;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kResThreads / 32;
+    const T *va = static_cast<const T *>(p.va);
+    const T *vc = static_cast<const T *>(p.vc);
+    const Meta *meta = static_cast<const Meta *>(p.meta);
+    T *xg = static_cast<T *>(p.x);
+
+    for (long long j = tid; j < n; j += kResThreads) {
+        x64s[j] = p.x64[j];
+        xs[j] = xg[j];
+    }
+    // control values and progress of the run, the same in every thread
+    const double lambda = st->lambda, eps = st->eps, rho = st->rho;
+    const long long max_iter = st->max_iter;
+    const int rule = st->rule, stop = st->stop, hold = st->hold_tick;
+    int force = st->force_step;
+    long long it = st->it, tick = st->tick;
+    int status = st->status, done = 0;
+    long long h_last = st->h;
+    double mv_last = st->maxviol, mn_last = st->maxnorm, mb_last = st->maxb;
+    double dxn = st->dx_norm, yn = st->y_norm;
+    const bool want_mn = stop == NSLI_STOP_EPSMEM, want_mb = stop == NSLI_STOP_MAXVIOL_REL;
+    const unsigned long long enc_neg_inf = sp_ord_enc(-INFINITY), enc_zero = sp_ord_enc(0.0);
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            sh_mv[q] = enc_neg_inf;
+            sh_mn[q] = enc_neg_inf;
+            sh_mb[q] = enc_zero;
+            sh_h[q] = 0;
+        }
+    }
+    __syncthreads();
+
+    for (int k = 0; k < iters && !done; ++k) {
+        const int par = k & 1;
+        const T tk = (T)((double)tick * rho);
+        int hc = 0;
+        double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+        auto row_done = [&](long long i, T dot) {
+            const Meta md = meta[i];
+            const T bi = fma(tk, (T)md.av, (T)md.b0);
+            const T ri = dot - bi;
+            const bool viol = ri > T(0);
+            cs[i] = viol ? ri * (T)md.inv_n2 : T(0);
+            hc += viol ? 1 : 0;
+            mv = fmax(mv, (double)ri);
+            if (want_mn)
+                mn = fmax(mn, (double)(ri * (T)md.inv_n));
+            if (want_mb)
+                mb = fmax(mb, (double)(bi < T(0) ? -bi : bi));
+        };
+        for (long long i = tid; i < m; i += kResThreads) {
+            const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
+            if (e1 - e0 > kResLong)
+                continue;
+            T acc = T(0);
+            for (long long e = e0; e < e1; ++e)
+                acc = fma(__ldg(va + e), xs[__ldg(p.ci + e)], acc);
+            row_done(i, acc);
+        }
+        for (int q = warp; q < p.n_res_long_rows; q += NW) {
+            const long long i = __ldg(p.res_long_rows + q);
+            const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
+            T acc = T(0);
+            for (long long e = e0 + lane; e < e1; e += 32)
+                acc = fma(__ldg(va + e), xs[__ldg(p.ci + e)], acc);
+            acc = warp_total(acc);
+            if (lane == 0)
+                row_done(i, acc);
+        }
+        // exact folds: integer sum, maxima as order-preserving integers
+        unsigned long long umv = sp_ord_enc(mv), umn = sp_ord_enc(mn), umb = sp_ord_enc(mb);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            hc += __shfl_xor_sync(0xffffffffu, hc, off);
+            umv = umax64(umv, __shfl_xor_sync(0xffffffffu, umv, off));
+            if (want_mn)
+                umn = umax64(umn, __shfl_xor_sync(0xffffffffu, umn, off));
+            if (want_mb)
+                umb = umax64(umb, __shfl_xor_sync(0xffffffffu, umb, off));
+        }
+        if (lane == 0) {
+            atomicAdd(&sh_h[par], hc);
+            atomicMax(&sh_mv[par], umv);
+            if (want_mn)
+                atomicMax(&sh_mn[par], umn);
+            if (want_mb)
+                atomicMax(&sh_mb[par], umb);
+        }
+        __syncthreads();
+        const long long H = sh_h[par];
+        h_last = H;
+        mv_last = sp_ord_dec(sh_mv[par]);
+        mn_last = sp_ord_dec(sh_mn[par]);
+        mb_last = sp_ord_dec(sh_mb[par]);
+        if (tid == 0) {   // slot of iteration k + 1 (its last readers passed a barrier since)
+            sh_h[par ^ 1] = 0;
+            sh_mv[par ^ 1] = enc_neg_inf;
+            sh_mn[par ^ 1] = enc_neg_inf;
+            sh_mb[par ^ 1] = enc_zero;
+        }
+        // stop decision (the grid kernels' rule), identical in every thread
+        {
+            const bool pass = !force && ((stop != NSLI_STOP_NONE && H == 0) ||
+                                         (stop == NSLI_STOP_EPSMEM && mn_last < eps) ||
+                                         (stop == NSLI_STOP_MAXVIOL_REL && mv_last <= eps * mb_last));
+            const bool at_max = !pass && it >= max_iter;
+            force = 0;
+            if (pass) {
+                status = ST_CANDIDATE;
+                done = 1;
+            } else if (at_max) {
+                status = NSLI_NOT_CONVERGED;
+                done = 1;
+            }
+            if (done)
+                break;
+        }
+
+        // columns: y_j in CSC order and the relaxed step, or ModAP's y_j
+        const double s_rel = H > 0 ? lambda / (double)H : 0.0;
+        const bool modap = rule == NSLI_RULE_MODAP;
+        auto col_done = [&](long long j, T y) -> double {
+            if (modap) {
+                const double yd = (double)y;
+                ys[j] = yd;
+                return yd * yd;
+            }
+            const double xo = x64s[j];
+            const double xn = xo - s_rel * (double)y;
+            x64s[j] = xn;
+            xs[j] = (T)xn;
+            const double d = xn - xo;
+            return d * d;
+        };
+        double part = 0.0;
+        for (long long j = tid; j < n; j += kResThreads) {
+            const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
+            if (e1 - e0 > kResLong)
+                continue;
+            T y = T(0);
+            for (long long e = e0; e < e1; ++e)
+                y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
+            part += col_done(j, y);
+        }
+        for (int q = warp; q < p.n_res_long_cols; q += NW) {
+            const long long j = __ldg(p.res_long_cols + q);
+            const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
+            T y = T(0);
+            for (long long e = e0 + lane; e < e1; e += 32)
+                y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
+            y = warp_total(y);
+            if (lane == 0)
+                part += col_done(j, y);
+        }
+        double dx2 = res_block_sum(part, sh_part, &sh_tot);
+        if (modap) {
+            yn = sqrt(dx2);
+            const double sm = yn > 0.0 ? lambda / yn : 0.0;
+            double part2 = 0.0;
+            for (long long j = tid; j < n; j += kResThreads) {
+                const double xo = x64s[j];
+                const double xn = xo - sm * ys[j];
+                x64s[j] = xn;
+                xs[j] = (T)xn;
+                const double d = xn - xo;
+                part2 += d * d;
+            }
+            dx2 = res_block_sum(part2, sh_part, &sh_tot);
+        } else {
+            yn = 0.0;
+        }
+        // the step's bookkeeping (the grid kernels' finish_step)
+        it += 1;
+        if (!hold)
+            tick += 1;
+        dxn = sqrt(dx2);
+        if (stop == NSLI_STOP_STEP && dxn < eps) {
+            status = NSLI_OK;
+            done = 1;
+        }
+    }
+    __syncthreads();
+    for (long long j = tid; j < n; j += kResThreads) {
+        p.x64[j] = x64s[j];
+        xg[j] = xs[j];
+    }
+    if (tid == 0) {
+        st->it = it;
+        st->tick = tick;
+        st->force_step = force;
+        st->h = h_last;
+        st->maxviol = mv_last;
+        st->maxnorm = mn_last;
+        st->maxb = mb_last;
+        st->dx_norm = dxn;
+        st->y_norm = yn;
+        st->status = status;
+        st->done = done;
+    }
+}
+
 template <typename T> int blocks_per_sm_row(int w)
 {
     int nb = 0;
@@ -628,6 +899,32 @@ cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const Spars
     return cudaGetLastError();
 }
 
+
+size_t sparse_resident_smem(bool f64, long long m, long long n)
+{
+    const size_t t = f64 ? 8 : 4;
+    return (size_t)n * (16 + t) + (size_t)m * t;
+}
+
+cudaError_t sparse_resident_prepare(bool f64, size_t smem)
+{
+    if (f64)
+        return cudaFuncSetAttribute(sparse_resident_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    return cudaFuncSetAttribute(sparse_resident_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t sparse_resident_launch(bool f64, cudaStream_t s, const SparseArgs &a, size_t smem, int iters)
+{
+    if (a.mode != 0 || smem > kResSmemMax)
+        return cudaErrorInvalidValue;
+    if (f64)
+        sparse_resident_kernel<double><<<1, kResThreads, smem, s>>>(a, iters);
+    else
+        sparse_resident_kernel<float><<<1, kResThreads, smem, s>>>(a, iters);
+    return cudaGetLastError();
+}
 
 cudaError_t sparse_rows_launch(bool f64, cudaStream_t s, const SparseArgs &a, long long row0, long long rows,
                                double *out)

@@ -76,7 +76,7 @@ def check_map_reduce(solver, A_eff, b, x, storage, tol_rel=1e-5):
 # ------------------------------------------------------------------ Map/Reduce
 
 SHAPES = [(1, 1), (7, 5), (300, 1), (150, 3), (1000, 333), (3001, 1000), (2000, 4100),
-          (600, 8192), (400, 16384)]
+          (600, 8192), (333, 8200), (700, 12000), (400, 16384)]
 
 
 @pytest.mark.parametrize("storage", STORAGES)
@@ -93,6 +93,23 @@ def test_map_reduce_one_step(storage, m, n):
         n2, _ = oracle.norms2(A_eff)
         np.testing.assert_allclose(s.norms2(), n2, rtol=1e-13)
         check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
+
+
+@pytest.mark.parametrize("n", [3000, 12000])
+@pytest.mark.parametrize("big", [40000.0, 2.0 ** 33])
+def test_fp8_large_x_and_slice_coefficients(n, big):
+    """FP8 decodes the odd element of each pair scaled by 2^-112 and carries
+    2^112 in its partner factor, except where that factor would not be
+    finite: a thread with an odd x entry of magnitude >= 2^15, a row with a
+    slice coefficient >= 2^15.  x entries of 40000 send some threads down
+    the plain decode; 2^33 also sends rows there.  Parity as everywhere."""
+    m = 1500
+    p = workloads.dense_system(m, n, seed=31 + n)
+    x = p["x0"].copy()
+    x[[1, 7, n // 2, n - 3]] = [big, -big, big, -big]
+    A_eff = stored_values(p["A"], "fp8")
+    with nsli.Solver(p["A"], p["b0"], x, Av=p["Av"], storage="fp8") as s:
+        check_map_reduce(s, A_eff, p["b0"], x, "fp8")
 
 
 @pytest.mark.parametrize("storage", STORAGES)

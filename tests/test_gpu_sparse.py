@@ -126,13 +126,16 @@ def test_sparse_stored_rows_and_model_system():
         check_one_step(s, p, "f64", p["b0"], np.zeros(p["m"]), p["x0"])
 
 
+@pytest.mark.parametrize("path", ["one-cta", "grid"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("rule", ["relaxed", "modap"])
 @pytest.mark.parametrize("rho", [0.0, 1e-3])
-def test_sparse_trajectory_matches_oracle(storage, rule, rho):
+def test_sparse_trajectory_matches_oracle(monkeypatch, path, storage, rule, rho):
     """Iterates agree to 1e-5 relative (1e-12 for binary64) at every
     iteration until the first Map with an ambiguous row (dense oracle on
-    the densified matrix)."""
+    the densified matrix); one iteration per call, so the one-CTA path
+    also carries its state across launches."""
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "1" if path == "one-cta" else "0")
     p = workloads.sparse_system(1500, 400, 12, seed=31 + int(rho * 1e4))
     A = workloads.csr_to_dense(p["rp"], p["ci"], p["val"], p["n"])
     n2, _ = oracle.norms2(A)
@@ -163,10 +166,14 @@ def test_sparse_trajectory_matches_oracle(storage, rule, rho):
         assert s.result()["tick"] == compared
 
 
+@pytest.mark.parametrize("path", ["one-cta", "grid"])
 @pytest.mark.parametrize("rule,lam", [("relaxed", 1.0), ("modap", 1.0)])
-def test_sparse_model_system_solve_matches_dense(rule, lam):
+def test_sparse_model_system_solve_matches_dense(monkeypatch, path, rule, lam):
     """Model system n = 256 in compressed form: the same solve as the dense
-    oracle (binary64, ||dx|| < 1e-8), iteration count within 1%."""
+    oracle (binary64, ||dx|| < 1e-8), iteration count within 1%, both on
+    one CTA (where this small system runs by default) and on the grid
+    kernels."""
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "1" if path == "one-cta" else "0")
     p = workloads.model_system_csr(256, seed=0)
     A = workloads.csr_to_dense(p["rp"], p["ci"], p["val"], p["n"])
     orule = oracle.RULE_RELAXED if rule == "relaxed" else oracle.RULE_MODAP
@@ -182,8 +189,10 @@ def test_sparse_model_system_solve_matches_dense(rule, lam):
     np.testing.assert_allclose(xg, ref["x"], rtol=0, atol=1e-6 * maxb)
 
 
+@pytest.mark.parametrize("path", ["one-cta", "grid"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_sparse_solve_to_feasibility(storage):
+def test_sparse_solve_to_feasibility(monkeypatch, path, storage):
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "1" if path == "one-cta" else "0")
     p = workloads.sparse_system(600, 150, 6, seed=41, x0_std=1.0)
     A = workloads.csr_to_dense(p["rp"], p["ci"], p["val"], p["n"])
     ref = oracle.solve(A, p["b0"], p["x0"], stop=oracle.STOP_MAXVIOL_REL, eps=1e-6, max_iter=400000)
@@ -195,7 +204,8 @@ def test_sparse_solve_to_feasibility(storage):
     assert res["max_viol"] <= 1e-6 * res["max_abs_b"]
 
 
-def test_sparse_graph_blocks_equal_single_launches_and_determinism():
+def test_sparse_graph_blocks_equal_single_launches_and_determinism(monkeypatch):
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "0")
     p = case("ragged")
     xs = []
     for block in (8, 1, 8):
@@ -211,7 +221,8 @@ def test_sparse_graph_blocks_equal_single_launches_and_determinism():
     np.testing.assert_array_equal(xs[0], xs[2])
 
 
-def test_sparse_launch_count():
+def test_sparse_launch_count(monkeypatch):
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "0")
     p = case("short-rows")
     with solver(p, "f32") as s:
         c0 = s.launch_count()
