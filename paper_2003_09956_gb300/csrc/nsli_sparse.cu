@@ -550,24 +550,43 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
     return a > b ? a : b;
 }
 
-// Fixed-order sum over the block (two barriers): every thread's value to
-// shared memory, warp 0 adds them lane-strided then by a butterfly.
-__device__ __forceinline__ double res_block_sum(double v, double *part, double *tot)
+// Running maximum for the row statistics.  Binary64: kept as the
+// order-preserving integer encoding, so no comparison goes to GB300's narrow
+// binary64 pipe; binary32: a plain fmaxf, encoded once at the end.
+template <typename T> struct ResMax;
+template <> struct ResMax<double> {
+    unsigned long long u;
+    __device__ __forceinline__ explicit ResMax(double init) : u(sp_ord_enc(init)) {}
+    __device__ __forceinline__ void add(double v) { u = umax64(u, sp_ord_enc(v)); }
+    __device__ __forceinline__ unsigned long long enc() const { return u; }
+};
+template <> struct ResMax<float> {
+    float f;
+    __device__ __forceinline__ explicit ResMax(double init) : f((float)init) {}
+    __device__ __forceinline__ void add(float v) { f = fmaxf(f, v); }
+    __device__ __forceinline__ unsigned long long enc() const { return sp_ord_enc((double)f); }
+};
+
+// r_i > 0 from the bit pattern (integer pipe); the same as the comparison
+// for every value but NaN, which the inputs exclude
+__device__ __forceinline__ bool positive(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool positive(float v) { return __float_as_int(v) > 0; }
+
+// Fixed-order sum of the block's per-thread values (called by warp 0):
+// a pairwise tree over each lane's kResThreads / 32 values, then a butterfly.
+__device__ __forceinline__ double res_fold(const double *part, int lane)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
-    part[tid] = v;
-    __syncthreads();
-    if (tid < 32) {
-        double t = 0.0;
+    constexpr int NW = kResThreads / 32;
+    double t[NW];
 #pragma unroll
-        for (int q = 0; q < kResThreads / 32; ++q)
-            t += part[lane + 32 * q];
-        t = warp_total(t);
-        if (lane == 0)
-            *tot = t;
-    }
-    __syncthreads();
-    return *tot;
+    for (int q = 0; q < NW; ++q)
+        t[q] = part[lane + 32 * q];
+#pragma unroll
+    for (int w = NW / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q)
+            t[q] += t[q + w];
+    return warp_total(t[0]);
 }
 
 template <typename T>
@@ -583,14 +602,18 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
     double *ys = x64s + n;
     T *xs = reinterpret_cast<T *>(ys + n);
     T *cs = xs + n;
-    // row statistics of iteration k accumulate in slot k & 1
-    __shared__ unsigned long long sh_mv[2], sh_mn[2], sh_mb[2];
-    __shared__ int sh_h[2];
+    constexpr int NW = kResThreads / 32;
+    __shared__ int sh_wh[NW];
+    __shared__ unsigned long long sh_wmv[NW], sh_wmn[NW], sh_wmb[NW];
     __shared__ double sh_part[kResThreads];
-    __shared__ double sh_tot;
+    // broadcast by thread 0: the run ended at a decision (read after the
+    // barrier that follows the gathers) or at a step (read after the next
+    // Map's barrier), the step scale, the next Map's tick term
+    __shared__ int sh_done_dec, sh_done_step;
+    __shared__ double sh_scale;
+    __shared__ T sh_tk;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kResThreads / 32;
     const T *va = static_cast<const T *>(p.va);
     const T *vc = static_cast<const T *>(p.vc);
     const Meta *meta = static_cast<const Meta *>(p.meta);
@@ -600,45 +623,54 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         x64s[j] = p.x64[j];
         xs[j] = xg[j];
     }
-    // control values and progress of the run, the same in every thread
+    // the run's control values; its progress is kept by thread 0
     const double lambda = st->lambda, eps = st->eps, rho = st->rho;
     const long long max_iter = st->max_iter;
     const int rule = st->rule, stop = st->stop, hold = st->hold_tick;
-    int force = st->force_step;
-    long long it = st->it, tick = st->tick;
-    int status = st->status, done = 0;
-    long long h_last = st->h;
-    double mv_last = st->maxviol, mn_last = st->maxnorm, mb_last = st->maxb;
-    double dxn = st->dx_norm, yn = st->y_norm;
+    const bool modap = rule == NSLI_RULE_MODAP;
     const bool want_mn = stop == NSLI_STOP_EPSMEM, want_mb = stop == NSLI_STOP_MAXVIOL_REL;
-    const unsigned long long enc_neg_inf = sp_ord_enc(-INFINITY), enc_zero = sp_ord_enc(0.0);
+    // ||dx|| < eps needs the square root only when dx^2 is not clearly above eps^2
+    const double eps2x4 = 4.0 * eps * eps;
+    const bool tiny_eps = eps * eps < 1e-300;
+    int force = 0, status = 0, done = 0;
+    long long it = 0, tick = 0, h_last = 0;
+    double mv_last = 0, mn_last = 0, mb_last = 0, dx2 = 0, yn = 0;
+    bool have_dx2 = false;
+    double dxn0 = 0;
     if (tid == 0) {
-        for (int q = 0; q < 2; ++q) {
-            sh_mv[q] = enc_neg_inf;
-            sh_mn[q] = enc_neg_inf;
-            sh_mb[q] = enc_zero;
-            sh_h[q] = 0;
-        }
+        force = st->force_step;
+        status = st->status;
+        it = st->it;
+        tick = st->tick;
+        h_last = st->h;
+        mv_last = st->maxviol;
+        mn_last = st->maxnorm;
+        mb_last = st->maxb;
+        dxn0 = st->dx_norm;
+        yn = st->y_norm;
+        sh_tk = (T)((double)tick * rho);
+        sh_done_dec = 0;
+        sh_done_step = 0;
     }
     __syncthreads();
 
-    for (int k = 0; k < iters && !done; ++k) {
-        const int par = k & 1;
-        const T tk = (T)((double)tick * rho);
+    for (int k = 0; k < iters; ++k) {
+        // ---- rows: r_i, c_i and the statistics of this thread's rows
+        const T tk = sh_tk;
         int hc = 0;
-        double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+        ResMax<T> mv(-INFINITY), mn(-INFINITY), mb(0.0);
         auto row_done = [&](long long i, T dot) {
             const Meta md = meta[i];
             const T bi = fma(tk, (T)md.av, (T)md.b0);
             const T ri = dot - bi;
-            const bool viol = ri > T(0);
+            const bool viol = positive(ri);
             cs[i] = viol ? ri * (T)md.inv_n2 : T(0);
             hc += viol ? 1 : 0;
-            mv = fmax(mv, (double)ri);
+            mv.add(ri);
             if (want_mn)
-                mn = fmax(mn, (double)(ri * (T)md.inv_n));
+                mn.add(ri * (T)md.inv_n);
             if (want_mb)
-                mb = fmax(mb, (double)(bi < T(0) ? -bi : bi));
+                mb.add(bi < T(0) ? -bi : bi);
         };
         for (long long i = tid; i < m; i += kResThreads) {
             const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
@@ -649,7 +681,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 acc = fma(__ldg(va + e), xs[__ldg(p.ci + e)], acc);
             row_done(i, acc);
         }
-        for (int q = warp; q < p.n_res_long_rows; q += NW) {
+        // long rows by warps, the last warp first (warp 0 has thread 0's work)
+        for (int q = NW - 1 - warp; q < p.n_res_long_rows; q += NW) {
             const long long i = __ldg(p.res_long_rows + q);
             const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
             T acc = T(0);
@@ -660,7 +693,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 row_done(i, acc);
         }
         // exact folds: integer sum, maxima as order-preserving integers
-        unsigned long long umv = sp_ord_enc(mv), umn = sp_ord_enc(mn), umb = sp_ord_enc(mb);
+        unsigned long long umv = mv.enc(), umn = mn.enc(), umb = mb.enc();
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             hc += __shfl_xor_sync(0xffffffffu, hc, off);
@@ -671,27 +704,30 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 umb = umax64(umb, __shfl_xor_sync(0xffffffffu, umb, off));
         }
         if (lane == 0) {
-            atomicAdd(&sh_h[par], hc);
-            atomicMax(&sh_mv[par], umv);
-            if (want_mn)
-                atomicMax(&sh_mn[par], umn);
-            if (want_mb)
-                atomicMax(&sh_mb[par], umb);
+            sh_wh[warp] = hc;
+            sh_wmv[warp] = umv;
+            sh_wmn[warp] = umn;
+            sh_wmb[warp] = umb;
         }
         __syncthreads();
-        const long long H = sh_h[par];
-        h_last = H;
-        mv_last = sp_ord_dec(sh_mv[par]);
-        mn_last = sp_ord_dec(sh_mn[par]);
-        mb_last = sp_ord_dec(sh_mb[par]);
-        if (tid == 0) {   // slot of iteration k + 1 (its last readers passed a barrier since)
-            sh_h[par ^ 1] = 0;
-            sh_mv[par ^ 1] = enc_neg_inf;
-            sh_mn[par ^ 1] = enc_neg_inf;
-            sh_mb[par ^ 1] = enc_zero;
-        }
-        // stop decision (the grid kernels' rule), identical in every thread
-        {
+        // the previous iteration's step rule (thread 0, after that barrier)
+        if (sh_done_step)
+            break;
+        // ---- the stop decision (the grid kernels' rule) by thread 0, while
+        // every thread gathers its y_j
+        if (tid == 0) {
+            long long H = 0;
+            unsigned long long a = sh_wmv[0], b = sh_wmn[0], c = sh_wmb[0];
+            for (int q = 0; q < NW; ++q) {
+                H += sh_wh[q];
+                a = umax64(a, sh_wmv[q]);
+                b = umax64(b, sh_wmn[q]);
+                c = umax64(c, sh_wmb[q]);
+            }
+            h_last = H;
+            mv_last = sp_ord_dec(a);
+            mn_last = sp_ord_dec(b);
+            mb_last = sp_ord_dec(c);
             const bool pass = !force && ((stop != NSLI_STOP_NONE && H == 0) ||
                                          (stop == NSLI_STOP_EPSMEM && mn_last < eps) ||
                                          (stop == NSLI_STOP_MAXVIOL_REL && mv_last <= eps * mb_last));
@@ -704,26 +740,10 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 status = NSLI_NOT_CONVERGED;
                 done = 1;
             }
-            if (done)
-                break;
+            sh_done_dec = done;
+            sh_scale = H > 0 ? lambda / (double)H : 0.0;
+            sh_tk = (T)((double)(hold ? tick : tick + 1) * rho);   // the next Map's
         }
-
-        // columns: y_j in CSC order and the relaxed step, or ModAP's y_j
-        const double s_rel = H > 0 ? lambda / (double)H : 0.0;
-        const bool modap = rule == NSLI_RULE_MODAP;
-        auto col_done = [&](long long j, T y) -> double {
-            if (modap) {
-                const double yd = (double)y;
-                ys[j] = yd;
-                return yd * yd;
-            }
-            const double xo = x64s[j];
-            const double xn = xo - s_rel * (double)y;
-            x64s[j] = xn;
-            xs[j] = (T)xn;
-            const double d = xn - xo;
-            return d * d;
-        };
         double part = 0.0;
         for (long long j = tid; j < n; j += kResThreads) {
             const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
@@ -732,9 +752,9 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
             T y = T(0);
             for (long long e = e0; e < e1; ++e)
                 y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
-            part += col_done(j, y);
+            ys[j] = (double)y;
         }
-        for (int q = warp; q < p.n_res_long_cols; q += NW) {
+        for (int q = NW - 1 - warp; q < p.n_res_long_cols; q += NW) {
             const long long j = __ldg(p.res_long_cols + q);
             const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
             T y = T(0);
@@ -742,33 +762,57 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
             y = warp_total(y);
             if (lane == 0)
-                part += col_done(j, y);
+                ys[j] = (double)y;
         }
-        double dx2 = res_block_sum(part, sh_part, &sh_tot);
+        __syncthreads();
+        if (sh_done_dec)
+            break;
+
+        // ---- the step: x_j -= lambda y_j / h (relaxed) or lambda y_j / ||y||
         if (modap) {
-            yn = sqrt(dx2);
-            const double sm = yn > 0.0 ? lambda / yn : 0.0;
-            double part2 = 0.0;
-            for (long long j = tid; j < n; j += kResThreads) {
-                const double xo = x64s[j];
-                const double xn = xo - sm * ys[j];
-                x64s[j] = xn;
-                xs[j] = (T)xn;
-                const double d = xn - xo;
-                part2 += d * d;
+            for (long long j = tid; j < n; j += kResThreads)
+                part += ys[j] * ys[j];
+            sh_part[tid] = part;
+            __syncthreads();
+            if (warp == 0) {
+                const double y2 = res_fold(sh_part, lane);
+                if (lane == 0) {
+                    yn = sqrt(y2);
+                    sh_scale = yn > 0.0 ? lambda / yn : 0.0;
+                }
             }
-            dx2 = res_block_sum(part2, sh_part, &sh_tot);
-        } else {
-            yn = 0.0;
+            __syncthreads();
+            part = 0.0;
         }
-        // the step's bookkeeping (the grid kernels' finish_step)
-        it += 1;
-        if (!hold)
-            tick += 1;
-        dxn = sqrt(dx2);
-        if (stop == NSLI_STOP_STEP && dxn < eps) {
-            status = NSLI_OK;
-            done = 1;
+        const double sc = sh_scale;
+        for (long long j = tid; j < n; j += kResThreads) {
+            const double xo = x64s[j];
+            const double xn = xo - sc * ys[j];
+            x64s[j] = xn;
+            xs[j] = (T)xn;
+            const double d = xn - xo;
+            part += d * d;
+        }
+        sh_part[tid] = part;
+        __syncthreads();
+        // ---- dx^2 folded by warp 0 and the step's bookkeeping (the grid
+        // kernels' finish_step) by thread 0, while the next Map runs
+        if (warp == 0) {
+            const double tot = res_fold(sh_part, lane);
+            if (lane == 0) {
+                it += 1;
+                if (!hold)
+                    tick += 1;
+                if (!modap)
+                    yn = 0.0;
+                dx2 = tot;
+                have_dx2 = true;
+                if (stop == NSLI_STOP_STEP && (tiny_eps || !(tot > eps2x4)) && sqrt(tot) < eps) {
+                    status = NSLI_OK;
+                    done = 1;
+                }
+                sh_done_step = done;
+            }
         }
     }
     __syncthreads();
@@ -784,7 +828,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         st->maxviol = mv_last;
         st->maxnorm = mn_last;
         st->maxb = mb_last;
-        st->dx_norm = dxn;
+        st->dx_norm = have_dx2 ? sqrt(dx2) : dxn0;
         st->y_norm = yn;
         st->status = status;
         st->done = done;
