@@ -589,6 +589,21 @@ __device__ __forceinline__ double res_fold(const double *part, int lane)
     return warp_total(t[0]);
 }
 
+// |v| as an integer that orders like |v| (the bits of a non-negative binary64)
+__device__ __forceinline__ long long abs_bits(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffll; }
+
+// GB300 executes a dependent binary64 operation in about 435 cycles (a
+// measured chain of FMAs on one SM, against about 12 for binary32), so an
+// iteration's time is set by the depth of its binary64 dependency chain, and
+// the kernel is arranged to keep that chain short: rows longer than
+// kResLong go to warps of their own (lanes hold four partial sums added in a
+// tree) while the other warps take the short rows two at a time; the tick
+// term of the next Map is formed during this one; the scalar decision uses a
+// table of lambda / h instead of a division; and the terms of ||dx||, which
+// no later step of the iteration needs, are formed after the barrier that
+// ends the step, their sum only when the step rule can hold (and for the
+// last step of a launch).
+
 template <typename T>
 __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const SparseArgs p, int iters)
 {
@@ -599,19 +614,20 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
     extern __shared__ __align__(16) unsigned char res_smem[];
     const long long n = p.n, m = p.m;
     double *x64s = reinterpret_cast<double *>(res_smem);
-    double *ys = x64s + n;
-    T *xs = reinterpret_cast<T *>(ys + n);
+    double *ys = x64s + n;                  // y_j; after the step, x_j before it
+    double *rtab = ys + n;                  // lambda / h for h = 0..m (0 for h = 0)
+    T *xs = reinterpret_cast<T *>(rtab + m + 1);
     T *cs = xs + n;
     constexpr int NW = kResThreads / 32;
     __shared__ int sh_wh[NW];
     __shared__ unsigned long long sh_wmv[NW], sh_wmn[NW], sh_wmb[NW];
-    __shared__ double sh_part[kResThreads];
-    // broadcast by thread 0: the run ended at a decision (read after the
-    // barrier that follows the gathers) or at a step (read after the next
-    // Map's barrier), the step scale, the next Map's tick term
-    __shared__ int sh_done_dec, sh_done_step;
+    __shared__ double sh_part[2][kResThreads];   // dx^2 (y^2) partials, by iteration parity
+    __shared__ long long sh_dmax[2][NW];         // max |dx_j| per warp (bits), by parity
+    // broadcast by thread 0: the run has ended, the step scale, the tick
+    // term of each Map (by iteration parity)
+    __shared__ int sh_done;
     __shared__ double sh_scale;
-    __shared__ T sh_tk;
+    __shared__ T sh_tk[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T *va = static_cast<const T *>(p.va);
@@ -619,23 +635,28 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
     const Meta *meta = static_cast<const Meta *>(p.meta);
     T *xg = static_cast<T *>(p.x);
 
-    for (long long j = tid; j < n; j += kResThreads) {
-        x64s[j] = p.x64[j];
-        xs[j] = xg[j];
-    }
     // the run's control values; its progress is kept by thread 0
     const double lambda = st->lambda, eps = st->eps, rho = st->rho;
     const long long max_iter = st->max_iter;
     const int rule = st->rule, stop = st->stop, hold = st->hold_tick;
     const bool modap = rule == NSLI_RULE_MODAP;
     const bool want_mn = stop == NSLI_STOP_EPSMEM, want_mb = stop == NSLI_STOP_MAXVIOL_REL;
-    // ||dx|| < eps needs the square root only when dx^2 is not clearly above eps^2
-    const double eps2x4 = 4.0 * eps * eps;
-    const bool tiny_eps = eps * eps < 1e-300;
+    for (long long j = tid; j < n; j += kResThreads) {
+        x64s[j] = p.x64[j];
+        xs[j] = xg[j];
+    }
+    for (long long h = tid; h <= m; h += kResThreads)
+        rtab[h] = h > 0 ? lambda / (double)h : 0.0;   // the grid kernels' lambda / h
+    // warps of their own for the long rows (columns), the last ones
+    const int lw_r = min(NW / 2, p.n_res_long_rows), lw_c = min(NW / 2, p.n_res_long_cols);
+    const int nt_r = (NW - lw_r) * 32, nt_c = (NW - lw_c) * 32;
+    // ||dx|| < eps is possible only if no |dx_j| exceeds eps (1e-6 of margin
+    // covers the rounding of the sum and the root)
+    const double gate = eps * (1.0 + 1e-6);
     int force = 0, status = 0, done = 0;
     long long it = 0, tick = 0, h_last = 0;
-    double mv_last = 0, mn_last = 0, mb_last = 0, dx2 = 0, yn = 0;
-    bool have_dx2 = false;
+    double mv_last = 0, mn_last = 0, mb_last = 0, yn = 0;
+    int last_par = -1;   // parity of the last step's dx^2 partials (thread 0)
     double dxn0 = 0;
     if (tid == 0) {
         force = st->force_step;
@@ -648,23 +669,40 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         mb_last = st->maxb;
         dxn0 = st->dx_norm;
         yn = st->y_norm;
-        sh_tk = (T)((double)tick * rho);
-        sh_done_dec = 0;
-        sh_done_step = 0;
+        sh_tk[0] = (T)((double)tick * rho);
+        sh_done = 0;
     }
     __syncthreads();
 
+    // warp 0: does the step rule hold after the step whose terms carry parity q?
+    auto step_rule = [&](int q) -> bool {
+        long long dm = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            dm = max(dm, sh_dmax[q][w]);
+        if (stop != NSLI_STOP_STEP || __longlong_as_double(dm) > gate)
+            return false;
+        return sqrt(res_fold(sh_part[q], lane)) < eps;
+    };
+
     for (int k = 0; k < iters; ++k) {
+        const int par = k & 1;
         // ---- rows: r_i, c_i and the statistics of this thread's rows
-        const T tk = sh_tk;
+        const T tk = sh_tk[par];
+        const bool tk0 = tk == T(0);   // b_i = fma(0, Av_i, b0_i) = b0_i
+        if (tid == 0)                  // the next Map's tick term
+            sh_tk[par ^ 1] = (T)((double)(hold ? tick : tick + 1) * rho);
         int hc = 0;
         ResMax<T> mv(-INFINITY), mn(-INFINITY), mb(0.0);
         auto row_done = [&](long long i, T dot) {
             const Meta md = meta[i];
-            const T bi = fma(tk, (T)md.av, (T)md.b0);
+            const T bi = tk0 ? (T)md.b0 : fma(tk, (T)md.av, (T)md.b0);
             const T ri = dot - bi;
             const bool viol = positive(ri);
-            cs[i] = viol ? ri * (T)md.inv_n2 : T(0);
+            T c = T(0);
+            if (viol)
+                c = ri * (T)md.inv_n2;
+            cs[i] = c;
             hc += viol ? 1 : 0;
             mv.add(ri);
             if (want_mn)
@@ -672,25 +710,49 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
             if (want_mb)
                 mb.add(bi < T(0) ? -bi : bi);
         };
-        for (long long i = tid; i < m; i += kResThreads) {
-            const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
-            if (e1 - e0 > kResLong)
-                continue;
-            T acc = T(0);
-            for (long long e = e0; e < e1; ++e)
-                acc = fma(__ldg(va + e), xs[__ldg(p.ci + e)], acc);
-            row_done(i, acc);
-        }
-        // long rows by warps, the last warp first (warp 0 has thread 0's work)
-        for (int q = NW - 1 - warp; q < p.n_res_long_rows; q += NW) {
-            const long long i = __ldg(p.res_long_rows + q);
-            const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
-            T acc = T(0);
-            for (long long e = e0 + lane; e < e1; e += 32)
-                acc = fma(__ldg(va + e), xs[__ldg(p.ci + e)], acc);
-            acc = warp_total(acc);
-            if (lane == 0)
-                row_done(i, acc);
+        if (tid < nt_r) {
+            // short rows, two at a time (independent chains)
+            for (long long i0 = tid; i0 < m; i0 += 2 * (long long)nt_r) {
+                const long long i1 = i0 + nt_r;
+                const long long a0 = __ldg(p.rp + i0), b0 = __ldg(p.rp + i0 + 1);
+                long long a1 = 0, b1 = 0;
+                if (i1 < m) {
+                    a1 = __ldg(p.rp + i1);
+                    b1 = __ldg(p.rp + i1 + 1);
+                }
+                const bool ok0 = b0 - a0 <= kResLong, ok1 = i1 < m && b1 - a1 <= kResLong;
+                const long long l0 = ok0 ? b0 - a0 : 0, l1 = ok1 ? b1 - a1 : 0;
+                T s0 = T(0), s1 = T(0);
+                for (long long q = 0; q < max(l0, l1); ++q) {
+                    if (q < l0)
+                        s0 = fma(__ldg(va + a0 + q), xs[__ldg(p.ci + a0 + q)], s0);
+                    if (q < l1)
+                        s1 = fma(__ldg(va + a1 + q), xs[__ldg(p.ci + a1 + q)], s1);
+                }
+                if (ok0)
+                    row_done(i0, s0);
+                if (ok1)
+                    row_done(i1, s1);
+            }
+        } else {
+            // long rows: four partial sums per lane, a tree, a butterfly
+            for (int q = warp - (NW - lw_r); q < p.n_res_long_rows; q += lw_r) {
+                const long long i = __ldg(p.res_long_rows + q);
+                const long long e0 = __ldg(p.rp + i), e1 = __ldg(p.rp + i + 1);
+                T a4[4] = {T(0), T(0), T(0), T(0)};
+                for (long long c = e0 + lane; c < e1; c += 128) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long e = c + 32 * u;
+                        if (e < e1)
+                            a4[u] = fma(__ldg(va + e), xs[__ldg(p.ci + e)], a4[u]);
+                    }
+                }
+                T acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+                acc = warp_total(acc);
+                if (lane == 0)
+                    row_done(i, acc);
+            }
         }
         // exact folds: integer sum, maxima as order-preserving integers
         unsigned long long umv = mv.enc(), umn = mn.enc(), umb = mb.enc();
@@ -710,115 +772,156 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
             sh_wmb[warp] = umb;
         }
         __syncthreads();
-        // the previous iteration's step rule (thread 0, after that barrier)
-        if (sh_done_step)
-            break;
-        // ---- the stop decision (the grid kernels' rule) by thread 0, while
-        // every thread gathers its y_j
-        if (tid == 0) {
-            long long H = 0;
-            unsigned long long a = sh_wmv[0], b = sh_wmn[0], c = sh_wmb[0];
-            for (int q = 0; q < NW; ++q) {
-                H += sh_wh[q];
-                a = umax64(a, sh_wmv[q]);
-                b = umax64(b, sh_wmn[q]);
-                c = umax64(c, sh_wmb[q]);
+        // ---- warp 0: the step rule of the previous step, then the stop
+        // decision (the grid kernels' rules), while the others gather y
+        if (warp == 0) {
+            const int lp = __shfl_sync(0xffffffffu, last_par, 0);
+            const bool step_stop = lp >= 0 && k > 0 && step_rule(lp);
+            if (lane == 0) {
+                if (step_stop) {
+                    status = NSLI_OK;
+                    done = 1;
+                } else {
+                    long long H = 0;
+                    unsigned long long a = sh_wmv[0], b = sh_wmn[0], c = sh_wmb[0];
+                    for (int q = 0; q < NW; ++q) {
+                        H += sh_wh[q];
+                        a = umax64(a, sh_wmv[q]);
+                        b = umax64(b, sh_wmn[q]);
+                        c = umax64(c, sh_wmb[q]);
+                    }
+                    h_last = H;
+                    mv_last = sp_ord_dec(a);
+                    mn_last = sp_ord_dec(b);
+                    mb_last = sp_ord_dec(c);
+                    const bool pass = !force && ((stop != NSLI_STOP_NONE && H == 0) ||
+                                                 (stop == NSLI_STOP_EPSMEM && mn_last < eps) ||
+                                                 (stop == NSLI_STOP_MAXVIOL_REL && mv_last <= eps * mb_last));
+                    const bool at_max = !pass && it >= max_iter;
+                    force = 0;
+                    if (pass) {
+                        status = ST_CANDIDATE;
+                        done = 1;
+                    } else if (at_max) {
+                        status = NSLI_NOT_CONVERGED;
+                        done = 1;
+                    }
+                    sh_scale = rtab[H];
+                }
+                sh_done = done;
             }
-            h_last = H;
-            mv_last = sp_ord_dec(a);
-            mn_last = sp_ord_dec(b);
-            mb_last = sp_ord_dec(c);
-            const bool pass = !force && ((stop != NSLI_STOP_NONE && H == 0) ||
-                                         (stop == NSLI_STOP_EPSMEM && mn_last < eps) ||
-                                         (stop == NSLI_STOP_MAXVIOL_REL && mv_last <= eps * mb_last));
-            const bool at_max = !pass && it >= max_iter;
-            force = 0;
-            if (pass) {
-                status = ST_CANDIDATE;
-                done = 1;
-            } else if (at_max) {
-                status = NSLI_NOT_CONVERGED;
-                done = 1;
-            }
-            sh_done_dec = done;
-            sh_scale = H > 0 ? lambda / (double)H : 0.0;
-            sh_tk = (T)((double)(hold ? tick : tick + 1) * rho);   // the next Map's
         }
-        double part = 0.0;
-        for (long long j = tid; j < n; j += kResThreads) {
-            const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
-            if (e1 - e0 > kResLong)
-                continue;
-            T y = T(0);
-            for (long long e = e0; e < e1; ++e)
-                y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
-            ys[j] = (double)y;
-        }
-        for (int q = NW - 1 - warp; q < p.n_res_long_cols; q += NW) {
-            const long long j = __ldg(p.res_long_cols + q);
-            const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
-            T y = T(0);
-            for (long long e = e0 + lane; e < e1; e += 32)
-                y = fma(__ldg(vc + e), cs[__ldg(p.ri + e)], y);
-            y = warp_total(y);
-            if (lane == 0)
+        // y_j in CSC order over the violated rows (c_i = 0 adds nothing)
+        if (tid < nt_c) {
+            for (long long j = tid; j < n; j += nt_c) {
+                const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
+                if (e1 - e0 > kResLong)
+                    continue;
+                T y = T(0);
+                for (long long e = e0; e < e1; ++e) {
+                    const T c = cs[__ldg(p.ri + e)];
+                    if (c != T(0))
+                        y = fma(__ldg(vc + e), c, y);
+                }
                 ys[j] = (double)y;
+            }
+        } else {
+            for (int q = warp - (NW - lw_c); q < p.n_res_long_cols; q += lw_c) {
+                const long long j = __ldg(p.res_long_cols + q);
+                const long long e0 = __ldg(p.cp + j), e1 = __ldg(p.cp + j + 1);
+                T y4[4] = {T(0), T(0), T(0), T(0)};
+                for (long long c = e0 + lane; c < e1; c += 128) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long e = c + 32 * u;
+                        if (e < e1) {
+                            const T cf = cs[__ldg(p.ri + e)];
+                            if (cf != T(0))
+                                y4[u] = fma(__ldg(vc + e), cf, y4[u]);
+                        }
+                    }
+                }
+                T y = (y4[0] + y4[1]) + (y4[2] + y4[3]);
+                y = warp_total(y);
+                if (lane == 0)
+                    ys[j] = (double)y;
+            }
         }
         __syncthreads();
-        if (sh_done_dec)
+        if (sh_done)
             break;
 
         // ---- the step: x_j -= lambda y_j / h (relaxed) or lambda y_j / ||y||
+        if (tid == 0) {
+            it += 1;
+            if (!hold)
+                tick += 1;
+            last_par = par;
+        }
         if (modap) {
+            double part = 0.0;
             for (long long j = tid; j < n; j += kResThreads)
                 part += ys[j] * ys[j];
-            sh_part[tid] = part;
+            sh_part[par][tid] = part;
             __syncthreads();
             if (warp == 0) {
-                const double y2 = res_fold(sh_part, lane);
+                const double y2 = res_fold(sh_part[par], lane);
                 if (lane == 0) {
                     yn = sqrt(y2);
                     sh_scale = yn > 0.0 ? lambda / yn : 0.0;
                 }
             }
             __syncthreads();
-            part = 0.0;
+        } else if (tid == 0) {
+            yn = 0.0;
         }
         const double sc = sh_scale;
         for (long long j = tid; j < n; j += kResThreads) {
+            const double yj = ys[j];
             const double xo = x64s[j];
-            const double xn = xo - sc * ys[j];
-            x64s[j] = xn;
-            xs[j] = (T)xn;
-            const double d = xn - xo;
-            part += d * d;
-        }
-        sh_part[tid] = part;
-        __syncthreads();
-        // ---- dx^2 folded by warp 0 and the step's bookkeeping (the grid
-        // kernels' finish_step) by thread 0, while the next Map runs
-        if (warp == 0) {
-            const double tot = res_fold(sh_part, lane);
-            if (lane == 0) {
-                it += 1;
-                if (!hold)
-                    tick += 1;
-                if (!modap)
-                    yn = 0.0;
-                dx2 = tot;
-                have_dx2 = true;
-                if (stop == NSLI_STOP_STEP && (tiny_eps || !(tot > eps2x4)) && sqrt(tot) < eps) {
-                    status = NSLI_OK;
-                    done = 1;
-                }
-                sh_done_step = done;
+            ys[j] = xo;
+            if (yj != 0.0) {   // x_j - sc * 0 = x_j
+                const double xn = xo - sc * yj;
+                x64s[j] = xn;
+                xs[j] = (T)xn;
             }
+        }
+        __syncthreads();
+        // the terms of ||dx|| (this thread's columns), for the step rule
+        // decided after the next Map's barrier
+        {
+            double part = 0.0;
+            long long dmax = 0;
+            for (long long j = tid; j < n; j += kResThreads) {
+                const double d = x64s[j] - ys[j];
+                part += d * d;
+                dmax = max(dmax, abs_bits(d));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+            sh_part[par][tid] = part;
+            if (lane == 0)
+                sh_dmax[par][warp] = dmax;
         }
     }
     __syncthreads();
     for (long long j = tid; j < n; j += kResThreads) {
         p.x64[j] = x64s[j];
         xg[j] = xs[j];
+    }
+    // the last step: its step rule (if the loop ended right after it) and ||dx||
+    double dxn = dxn0;
+    if (warp == 0) {
+        const int lp = __shfl_sync(0xffffffffu, last_par, 0);
+        const int dn = __shfl_sync(0xffffffffu, done, 0);
+        if (lp >= 0) {
+            if (!dn && step_rule(lp) && lane == 0) {
+                status = NSLI_OK;
+                done = 1;
+            }
+            dxn = sqrt(res_fold(sh_part[lp], lane));
+        }
     }
     if (tid == 0) {
         st->it = it;
@@ -828,7 +931,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         st->maxviol = mv_last;
         st->maxnorm = mn_last;
         st->maxb = mb_last;
-        st->dx_norm = have_dx2 ? sqrt(dx2) : dxn0;
+        st->dx_norm = dxn;
         st->y_norm = yn;
         st->status = status;
         st->done = done;
@@ -947,7 +1050,7 @@ cudaError_t sparse_verify_launch(bool f64, int grid, cudaStream_t s, const Spars
 size_t sparse_resident_smem(bool f64, long long m, long long n)
 {
     const size_t t = f64 ? 8 : 4;
-    return (size_t)n * (16 + t) + (size_t)m * t;
+    return (size_t)n * (16 + t) + (size_t)m * t + (size_t)(m + 1) * 8;
 }
 
 cudaError_t sparse_resident_prepare(bool f64, size_t smem)
