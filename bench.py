@@ -90,6 +90,9 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the serving stream measured in the same run (0: none)")
     ap.add_argument("--serving-only", action="store_true", help="time only the serving stream")
+    ap.add_argument("--model-only", action="store_true",
+                    help="time only the model system's solves (dense and compressed rows)")
+    ap.add_argument("--model-seeds", type=int, default=30, help="seeds of the model-system solves")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -568,6 +571,15 @@ def main():
             print(json.dumps({"metric": "serving solves/sec", "value": r["solves_per_s"], "unit": "solves/s",
                               "config": {"workload": "poisson-200/s mixed-size bf16 stream"}, **r}), flush=True)
         return 0
+    if args.model_only:
+        dense = time_model_system(nsli, seeds=args.model_seeds)
+        csr = time_model_system_csr(nsli, seeds=args.model_seeds)
+        if rank == 0:
+            print(json.dumps({"metric": "model system p50 solve ms", "value": csr["p50_solve_ms"], "unit": "ms",
+                              "higher_is_better": False,
+                              "config": {"workload": "model system n=256 m=513 f64, STEP 1e-8"},
+                              "compressed_rows_one_cta": csr, "dense_rows_grid": dense}), flush=True)
+        return 0
     if args.sparse_only:
         peak, _ = measured_peak()
         r = time_sparse(nsli, torch, args.sparse, args.steps, max(3, args.warmup), peak)
@@ -634,8 +646,8 @@ def main():
                         "map_frac_of_measured_hbm": vb / (r["map_ms_avg"] / 1000.0) / 1e9 / peak,
                         "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
 
-    variants["model_system_f64"] = time_model_system(nsli)
-    variants["model_system_f64_csr"] = time_model_system_csr(nsli)
+    variants["model_system_f64"] = time_model_system(nsli, seeds=args.model_seeds)
+    variants["model_system_f64_csr"] = time_model_system_csr(nsli, seeds=args.model_seeds)
     if args.sparse:
         variants["sparse_f32"] = time_sparse(nsli, torch, args.sparse, K, W, peak)
     if args.matrix_updates:

@@ -1245,7 +1245,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     r.iters = h->st_host->it;
     r.tick = h->st_host->tick;
     r.status = status;
-    r.last_step_norm = h->st_host->dx_norm;
+    r.last_step_norm = std::sqrt(h->st_host->dx2);
     h->last_check = r;
     if (out)
         *out = r;
@@ -1392,7 +1392,7 @@ int nsli_get_result(nsli_handle h, nsli_result *out)
     r.tick = h->st_host->tick;
     const int sst = h->st_host->status;
     r.status = (sst == ST_RUNNING || sst == ST_CANDIDATE) ? NSLI_NOT_CONVERGED : sst;
-    r.last_step_norm = h->st_host->dx_norm;
+    r.last_step_norm = std::sqrt(h->st_host->dx2);
     *out = r;
     return NSLI_OK;
 }

@@ -50,8 +50,21 @@ struct DevState {
     int error;            // ERRF_* bits
     unsigned int ticket;  // last-block counter of the reduce kernel
     long long h;          // stats of the last Map
-    double maxviol, maxnorm, maxb, dx_norm, y_norm;
+    double maxviol, maxnorm, maxb;
+    double dx2;           // ||dx||^2 of the last step (its root is taken by the host)
+    double y_norm;
 };
+
+// The step rule ||dx|| < eps from ||dx||^2 (binary64 square roots are long
+// dependency chains on GB300): the root is needed only when dx^2 is not
+// above 4 eps^2, i.e. when ||dx|| could be below eps.
+__host__ __device__ __forceinline__ bool step_norm_below(double dx2, double eps)
+{
+    const double e2 = eps * eps;
+    if (dx2 > 4.0 * e2 && !(e2 < 1e-300))
+        return false;
+    return sqrt(dx2) < eps;
+}
 
 enum : int { ST_RUNNING = 2, ST_CANDIDATE = 3 };
 enum : int { ERRF_TIMEOUT = 1 };

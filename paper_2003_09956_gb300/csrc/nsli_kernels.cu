@@ -757,10 +757,13 @@ const void *long_fn(int storage, int rg, bool sy)
 // ---------------------------------------------------- reduce and update ----
 //
 // Block = 256 threads = 8 groups x 32 columns.  Group q sums partial rows
-// g = q, q + 8, ... of its column in binary64; the 8 group sums are added in
-// order 0..7.  Every block recomputes h and the maxima from the per-CTA
-// records (exact integer sum / exact maxima), so all blocks take the same
-// decision.  The last block to finish (ticket) completes the step.
+// g = q, q + 8, ... of its column in the accumulation type, and the 8 group
+// sums are added in binary64: in order 0..7 for binary32 storage; for
+// binary64 storage, whose dependent operations are slow on GB300, as four
+// running sums per group and trees.  Every block recomputes h and the maxima
+// from the per-CTA records (exact integer sum / exact maxima), so all blocks
+// take the same decision.  The last block to finish (ticket) completes the
+// step.
 struct ReduceShared {
     double part[8][32];
     double red[8];
@@ -769,32 +772,45 @@ struct ReduceShared {
     int last;
 };
 
+__device__ __forceinline__ unsigned long long red_ord_enc(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double red_ord_dec(unsigned long long u)
+{
+    const unsigned long long bits = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceShared &sh)
 {
     const int lane = threadIdx.x & 31;
+    // maxima as order-preserving integers: exact, and no binary64 compare
+    // (a long dependency chain on GB300) on the way
     if (threadIdx.x < 32) {
         long long h = 0;
-        double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
+        unsigned long long mv = red_ord_enc(-INFINITY), mn = mv, mb = red_ord_enc(0.0);
 #pragma unroll 4
         for (int g = lane; g < G; g += 32) {
             const PartStat q = ps[g];
             h += q.h;
-            mv = fmax(mv, q.maxviol);
-            mn = fmax(mn, q.maxnorm);
-            mb = fmax(mb, q.maxb);
+            mv = max(mv, red_ord_enc(q.maxviol));
+            mn = max(mn, red_ord_enc(q.maxnorm));
+            mb = max(mb, red_ord_enc(q.maxb));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             h += __shfl_xor_sync(0xffffffffu, h, off);
-            mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, off));
-            mn = fmax(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+            mv = max(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+            mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
         }
         if (lane == 0) {
             sh.h = h;
-            sh.mv = mv;
-            sh.mn = mn;
-            sh.mb = mb;
+            sh.mv = red_ord_dec(mv);
+            sh.mn = red_ord_dec(mn);
+            sh.mb = red_ord_dec(mb);
         }
     }
 }
@@ -830,20 +846,38 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             // the partial rows g = grp, grp + 8, ... added in that order in
             // the accumulation type (binary64 is slow on this part), the
             // eight group sums then in binary64
-            Acc t = Acc(0);
+            if constexpr (sizeof(Acc) == 8) {
+                // binary64: four running sums (g = grp + 8 (4c + u)), added
+                // in a tree; a dependent binary64 add costs ~435 cycles here
+                double a[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int g = grp; g < p.G; g += 32) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (g + 8 * u < p.G)
+                            a[u] += py[(long long)(g + 8 * u) * p.ld + j];
+                }
+                yj = (a[0] + a[1]) + (a[2] + a[3]);
+            } else {
+                Acc t = Acc(0);
 #pragma unroll 8
-            for (int g = grp; g < p.G; g += 8)
-                t += py[(long long)g * p.ld + j];
-            yj = (double)t;
+                for (int g = grp; g < p.G; g += 8)
+                    t += py[(long long)g * p.ld + j];
+                yj = (double)t;
+            }
         }
         sh.part[grp][lane] = yj;
     }
     __syncthreads();
     if (step && grp == 0) {
         double y = 0.0;
+        if constexpr (sizeof(Acc) == 8) {
+            y = ((sh.part[0][lane] + sh.part[1][lane]) + (sh.part[2][lane] + sh.part[3][lane])) +
+                ((sh.part[4][lane] + sh.part[5][lane]) + (sh.part[6][lane] + sh.part[7][lane]));
+        } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            y += sh.part[q][lane];
+            for (int q = 0; q < 8; ++q)
+                y += sh.part[q][lane];
+        }
         double val = 0.0;
         if (j < p.ld) {
             if (rule == NSLI_RULE_MODAP) {
@@ -928,9 +962,9 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             st->it += 1;
             if (!st->hold_tick)
                 st->tick += 1;
-            st->dx_norm = sqrt(dx2);
+            st->dx2 = dx2;
             st->y_norm = ynorm;
-            if (stop == NSLI_STOP_STEP && sqrt(dx2) < eps) {
+            if (stop == NSLI_STOP_STEP && step_norm_below(dx2, eps)) {
                 st->status = NSLI_OK;
                 st->done = 1;
             }

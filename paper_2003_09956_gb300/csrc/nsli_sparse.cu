@@ -215,9 +215,9 @@ __device__ void finish_step(DevState *st, double dx2, double ynorm)
     st->it += 1;
     if (!st->hold_tick)
         st->tick += 1;
-    st->dx_norm = sqrt(dx2);
+    st->dx2 = dx2;
     st->y_norm = ynorm;
-    if (st->stop == NSLI_STOP_STEP && sqrt(dx2) < st->eps) {
+    if (st->stop == NSLI_STOP_STEP && step_norm_below(dx2, st->eps)) {
         st->status = NSLI_OK;
         st->done = 1;
     }
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
     long long it = 0, tick = 0, h_last = 0;
     double mv_last = 0, mn_last = 0, mb_last = 0, yn = 0;
     int last_par = -1;   // parity of the last step's dx^2 partials (thread 0)
-    double dxn0 = 0;
+    double dx2_0 = 0;
     if (tid == 0) {
         force = st->force_step;
         status = st->status;
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         mv_last = st->maxviol;
         mn_last = st->maxnorm;
         mb_last = st->maxb;
-        dxn0 = st->dx_norm;
+        dx2_0 = st->dx2;
         yn = st->y_norm;
         sh_tk[0] = (T)((double)tick * rho);
         sh_done = 0;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
             dm = max(dm, sh_dmax[q][w]);
         if (stop != NSLI_STOP_STEP || __longlong_as_double(dm) > gate)
             return false;
-        return sqrt(res_fold(sh_part[q], lane)) < eps;
+        return step_norm_below(res_fold(sh_part[q], lane), eps);
     };
 
     for (int k = 0; k < iters; ++k) {
@@ -910,8 +910,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         p.x64[j] = x64s[j];
         xg[j] = xs[j];
     }
-    // the last step: its step rule (if the loop ended right after it) and ||dx||
-    double dxn = dxn0;
+    // the last step: its step rule (if the loop ended right after it) and ||dx||^2
+    double dx2 = dx2_0;
     if (warp == 0) {
         const int lp = __shfl_sync(0xffffffffu, last_par, 0);
         const int dn = __shfl_sync(0xffffffffu, done, 0);
@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 status = NSLI_OK;
                 done = 1;
             }
-            dxn = sqrt(res_fold(sh_part[lp], lane));
+            dx2 = res_fold(sh_part[lp], lane);
         }
     }
     if (tid == 0) {
@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
         st->maxviol = mv_last;
         st->maxnorm = mn_last;
         st->maxb = mb_last;
-        st->dx_norm = dxn;
+        st->dx2 = dx2;
         st->y_norm = yn;
         st->status = status;
         st->done = done;
