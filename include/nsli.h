@@ -82,7 +82,9 @@ typedef struct {
     int32_t stop;        /* NSLI_STOP_*                                             */
     double eps;          /* threshold of the stopping rule, >= 0                   */
     int64_t max_iter;    /* nsli_solve: maximum number of x-updates, >= 0           */
-    int32_t block_iters; /* iterations per captured CUDA graph; 0 selects 32        */
+    int32_t block_iters; /* iterations per captured CUDA graph (0: 32); for a small
+                            sparse system run on one CTA, iterations per launch
+                            (0: 1024)                                                */
     int32_t reserved;    /* must be 0                                               */
     double rho;          /* translation per tick: b(k) = b0 + k * rho * Av          */
 } nsli_params;
@@ -149,7 +151,14 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage,
  * copied and checked on the host; nothing is retained.  Every other call
  * on the handle works as for a dense one, except nsli_test_inject_timeout
  * (NSLI_ERR_UNSUPPORTED); a ModAP iteration is three kernel launches
- * instead of two.  Errors: NSLI_ERR_ARG (sizes < 1, NULL required pointer,
+ * instead of two.  A small system (x, the coefficients and a table of
+ * lambda / h fit in one CTA's shared memory, and the matrix fits with them in
+ * one SM's on-chip memory) is iterated by nsli_iterate and nsli_solve on one
+ * CTA, a whole block of iterations per launch (same steps and decisions; its
+ * own fixed summation order, so not bit-identical to the grid kernels, and
+ * bit-identical however a run is split into launches); the environment
+ * variable NSLI_SPARSE_RESIDENT=0 (=1) at creation turns this off (forces
+ * it wherever the shared memory suffices).  Errors: NSLI_ERR_ARG (sizes < 1, NULL required pointer,
  * malformed offsets or indices), NSLI_ERR_UNSUPPORTED (storage, m or n
  * >= 2^31), NSLI_ERR_ZERO_ROW (an empty or all-zero row),
  * NSLI_ERR_NONFINITE, NSLI_ERR_OOM, NSLI_ERR_CUDA.  On error *out is NULL
