@@ -59,6 +59,11 @@ struct nsli_solver {
     VerOut *ver = nullptr;
     int *flags = nullptr;
 
+    // lambda / h, h = 0..m, for the relaxed step (filled when a run begins
+    // with a step size other than the one it holds)
+    double *rtab = nullptr;
+    double rtab_lambda = std::nan("");
+
     DevState *st_host = nullptr;  // pinned
     VerOut *ver_host = nullptr;   // pinned
     int *flags_host = nullptr;    // pinned
@@ -132,7 +137,7 @@ void free_all(nsli_solver *h)
                    (h->x64 != h->x) ? (void *)h->x64 : nullptr,
                    (h->n2_meta != h->n2_64) ? (void *)h->n2_meta : nullptr,
                    h->rp, h->cp, h->ci, h->ri, h->row_cnt, h->col_cnt, h->row_pieces, h->col_pieces,
-                   h->va, h->vc, h->coef, h->row_slots, h->col_slots, h->res_rows, h->res_cols};
+                   h->va, h->vc, h->coef, h->row_slots, h->col_slots, h->res_rows, h->res_cols, h->rtab};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -253,6 +258,7 @@ ReduceArgs reduce_args(nsli_solver *h)
     a.ybuf = h->ybuf;
     a.part_dx = h->part_dx;
     a.st = h->st;
+    a.rtab = h->rtab;
     a.ld = h->ld;
     a.G = h->G;
     return a;
@@ -419,7 +425,12 @@ int begin_run(nsli_solver *h, const nsli_params *p, int stop, long long max_iter
     b.reset_it = 1;
     b.force_step = 0;
     b.tick = -1;
+    const bool fill = h->rtab && !(h->rtab_lambda == p->lambda);
+    b.rtab = fill ? h->rtab : nullptr;
+    b.rtab_m = h->m;
     CK(state_begin_launch(h->stream, h->st, b), "begin run");
+    if (fill)
+        h->rtab_lambda = p->lambda;
     h->launches += 1;
     return NSLI_OK;
 }
@@ -516,6 +527,7 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
         CKC(cudaMalloc((void **)&h->x64, (size_t)h->ld * 8), "allocate binary64 x");
     CKC(cudaMalloc(&h->part_y, (size_t)h->G * h->ld * accb), "allocate partial sums");
     CKC(cudaMalloc((void **)&h->part_stat, (size_t)h->G * sizeof(PartStat)), "allocate partial stats");
+    CKC(cudaMalloc((void **)&h->rtab, (size_t)(m + 1) * 8), "allocate step table");
     CKC(cudaMalloc((void **)&h->part_dx, (size_t)h->red_grid * 8), "allocate step partials");
     CKC(cudaMalloc((void **)&h->ybuf, (size_t)h->ld * 8), "allocate y");
     CKC(cudaMalloc((void **)&h->dtmp, (size_t)std::max<long long>(m, h->ld) * 8), "allocate staging");
@@ -847,6 +859,7 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     else
         CKC(cudaMalloc((void **)&h->x64, (size_t)n * 8), "allocate binary64 x");
     CKC(cudaMalloc((void **)&h->part_stat, (size_t)g_row * sizeof(PartStat)), "allocate partial stats");
+    CKC(cudaMalloc((void **)&h->rtab, (size_t)(m + 1) * 8), "allocate step table");
     CKC(cudaMalloc((void **)&h->part_dx, (size_t)g_col * 8), "allocate step partials");
     CKC(cudaMalloc((void **)&h->ybuf, (size_t)n * 8), "allocate y");
     CKC(cudaMalloc((void **)&h->dtmp, (size_t)std::max<long long>(m, n) * 8), "allocate staging");
@@ -905,6 +918,7 @@ int nsli_create_csr(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int
     sp.st = h->st;
     sp.ignore_done = 0;
     sp.mode = 0;
+    sp.rtab = h->rtab;
     if (h->resident) {
         if (!long_rows.empty()) {
             CKC(cudaMalloc((void **)&h->res_rows, long_rows.size() * 4), "allocate long row list");
@@ -1456,7 +1470,7 @@ long long problem_bytes(int storage, long long m, long long n, int num_sms)
     const int eb = storage == NSLI_F64 ? 8 : storage == NSLI_F32 ? 4 : storage == NSLI_BF16 ? 2 : 1;
     const long long ld = n + 16;
     const long long G = std::min<long long>(num_sms, m);
-    return m * ld * eb + m * (32 + 4 * 8 + 4) + G * ld * 8 + ld * 40 + (1 << 16);
+    return m * ld * eb + m * (32 + 5 * 8 + 4) + G * ld * 8 + ld * 40 + (1 << 16);
 }
 
 int items_of(nsli_solver *h)

@@ -104,6 +104,7 @@ struct ReduceArgs {
     double *ybuf;
     double *part_dx;
     DevState *st;
+    const double *rtab;    // lambda / h for h = 0..m (written when a run begins); NULL: divide
     long long ld;
     int G;
 };
@@ -224,6 +225,8 @@ struct StateBegin {
     int reset_it;        // 1: it = 0
     int force_step;
     long long tick;      // >= 0: set the tick
+    double *rtab;        // non-NULL: write lambda / h to rtab[h], h = 0..rtab_m (0 for h = 0)
+    long long rtab_m;
 };
 cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b);
 cudaError_t state_resume_launch(cudaStream_t s, DevState *st);
@@ -276,6 +279,7 @@ struct SparseArgs {
     int w_row, w_col;         // lanes per row / column (1, 2, 4, ..., 32)
     int ignore_done;          // run even when the done flag is set
     int mode;                 // 0: iteration; 1: Map and y only (no decision, no step)
+    const double *rtab;       // lambda / h for h = 0..m (written when a run begins)
     // one-CTA runs of small systems (sparse_resident_kernel): the rows and
     // columns with more than kResLong entries, taken by one warp each
     const int *res_long_rows, *res_long_cols;

@@ -884,7 +884,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
                 p.ybuf[j] = y;
                 val = y * y;
             } else {
-                const double s = h > 0 ? lambda / (double)h : 0.0;
+                const double s = h > 0 ? (p.rtab ? __ldg(p.rtab + h) : lambda / (double)h) : 0.0;
                 const double xo = p.x64[j];
                 const double xn = xo - s * y;
                 p.x64[j] = xn;
@@ -1243,8 +1243,18 @@ __global__ void check_finite_kernel(const double *v, long long n, int *flags)
         atomicOr(flags, PREPF_NONFINITE);
 }
 
+// Run parameters into the state (block 0, thread 0) and, when the step size
+// changed, the table lambda / h that the step reads instead of dividing (a
+// binary64 division is a long dependency chain on GB300).
 __global__ void state_begin_kernel(DevState *st, const StateBegin b)
 {
+    if (b.rtab) {
+        for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h <= b.rtab_m;
+             h += (long long)gridDim.x * blockDim.x)
+            b.rtab[h] = h > 0 ? b.lambda / (double)h : 0.0;
+    }
+    if (blockIdx.x != 0 || threadIdx.x != 0)
+        return;
     st->lambda = b.lambda;
     st->eps = b.eps;
     st->rho = b.rho;
@@ -1492,7 +1502,10 @@ cudaError_t check_finite_launch(cudaStream_t s, const double *v, long long n, in
 
 cudaError_t state_begin_launch(cudaStream_t s, DevState *st, const StateBegin &b)
 {
-    state_begin_kernel<<<1, 1, 0, s>>>(st, b);
+    long long blocks = b.rtab ? (b.rtab_m + 256) / 256 : 1;
+    if (blocks > 1024)
+        blocks = 1024;
+    state_begin_kernel<<<(unsigned)blocks, b.rtab ? 256 : 1, 0, s>>>(st, b);
     return cudaGetLastError();
 }
 

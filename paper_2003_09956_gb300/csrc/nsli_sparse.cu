@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kU = kSparseU;
+static_assert(kU > 0 && (kU & (kU - 1)) == 0, "loads per lane: a power of two");
 
 template <typename T> struct SpTraits;
 template <> struct SpTraits<double> {
@@ -60,7 +61,9 @@ template <typename T> __device__ __forceinline__ T warp_total(T v)
     return v;
 }
 
-// Block sum in a fixed tree: warp butterflies, then the 8 warp sums in order.
+// Block sum in a fixed tree: warp butterflies, then a pairwise tree over the
+// 8 warp sums (GB300 takes about 435 cycles per dependent binary64 add, so
+// every sum here is a tree rather than a chain).
 template <typename T> __device__ __forceinline__ T block_sum(T v, T *sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -69,20 +72,31 @@ template <typename T> __device__ __forceinline__ T block_sum(T v, T *sh)
     if (lane == 0)
         sh[warp] = v;
     __syncthreads();
-    T t = T(0);
+    constexpr int NW = kThreads / 32;
+    T t[NW];
 #pragma unroll
-    for (int q = 0; q < kThreads / 32; ++q)
-        t += sh[q];
-    return t;
+    for (int q = 0; q < NW; ++q)
+        t[q] = sh[q];
+#pragma unroll
+    for (int w = NW / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q)
+            t[q] += t[q + w];
+    return t[0];
 }
 
 // sum over e in [e0, e1) of val[e] * g[idx[e]] for lane l of a group of W
 // lanes: chunks of W * kU entries, lane l taking e = c + l + u W, the kU
-// loads of a chunk issued before any of its products; lane-local order.
+// loads of a chunk issued before any of its products; binary64 adds slot u
+// of every chunk into running sum u and the kU sums in a fixed tree,
+// binary32 adds everything into one running sum in lane-local order.
 template <typename T, int W>
 __device__ __forceinline__ T seg_dot(long long e0, long long e1, const int *idx, const T *val, const T *g, int l)
 {
-    T acc = T(0);
+    T acc[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+        acc[u] = T(0);
     for (long long c = e0; c < e1; c += (long long)W * kU) {
         int id[kU];
         T v[kU];
@@ -97,11 +111,24 @@ __device__ __forceinline__ T seg_dot(long long e0, long long e1, const int *idx,
 #pragma unroll
         for (int u = 0; u < kU; ++u)
             gv[u] = __ldg(g + id[u]);
+        if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            acc = fma(v[u], gv[u], acc);
+            for (int u = 0; u < kU; ++u)
+                acc[u] = fma(v[u], gv[u], acc[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                acc[0] = fma(v[u], gv[u], acc[0]);
+        }
     }
-    return acc;
+    // binary64: the kU running sums (one per load slot) in a fixed pairwise
+    // tree; binary32 keeps one running sum (its latency is short)
+#pragma unroll
+    for (int w = kU / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int u = 0; u < w; ++u)
+            acc[u] += acc[u + w];
+    return acc[0];
 }
 
 // One piece of a heavy row / column: the block's sum over the piece, then
@@ -127,10 +154,12 @@ __device__ __forceinline__ bool heavy_piece(const SegPiece &pc, const int *idx, 
     if (!*sh_flag)
         return false;
     __threadfence();
+    // the segment's piece sums: thread t adds pieces t, t + kThreads, ...,
+    // then the block tree (the same order whichever block finishes last)
     T t = T(0);
-    for (int q = 0; q < pc.npieces; ++q)
+    for (int q = threadIdx.x; q < pc.npieces; q += kThreads)
         t += __ldcg(slots + pc.first + q);
-    *total = t;
+    *total = block_sum(t, sh_sum);
     if (threadIdx.x == 0)
         cnt[pc.hs] = 0;   // ready for the next launch
     return true;
@@ -141,30 +170,47 @@ struct StatAcc {
     double mv, mn, mb;
 };
 
+// Order-preserving integer image of a binary64 value (and back): maxima
+// folded on the integer pipe are exact and add no binary64 latency.
+__device__ __forceinline__ unsigned long long stat_enc(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double stat_dec(unsigned long long u)
+{
+    const unsigned long long bits = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    return __longlong_as_double((long long)bits);
+}
+
 // Fold per-thread stats into one record (exact: integer sum and maxima).
 __device__ StatAcc block_stats(StatAcc s, StatAcc *sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long mv = stat_enc(s.mv), mn = stat_enc(s.mn), mb = stat_enc(s.mb);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         s.h += __shfl_xor_sync(0xffffffffu, s.h, off);
-        s.mv = fmax(s.mv, __shfl_xor_sync(0xffffffffu, s.mv, off));
-        s.mn = fmax(s.mn, __shfl_xor_sync(0xffffffffu, s.mn, off));
-        s.mb = fmax(s.mb, __shfl_xor_sync(0xffffffffu, s.mb, off));
+        mv = max(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+        mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
     }
     __syncthreads();
     if (lane == 0)
-        sh[warp] = s;
+        sh[warp] = StatAcc{s.h, stat_dec(mv), stat_dec(mn), stat_dec(mb)};
     __syncthreads();
-    StatAcc t{0, -INFINITY, -INFINITY, 0.0};
+    long long h = 0;
+    mv = stat_enc(-INFINITY);
+    mn = mv;
+    mb = stat_enc(0.0);
 #pragma unroll
     for (int q = 0; q < kThreads / 32; ++q) {
-        t.h += sh[q].h;
-        t.mv = fmax(t.mv, sh[q].mv);
-        t.mn = fmax(t.mn, sh[q].mn);
-        t.mb = fmax(t.mb, sh[q].mb);
+        h += sh[q].h;
+        mv = max(mv, stat_enc(sh[q].mv));
+        mn = max(mn, stat_enc(sh[q].mn));
+        mb = max(mb, stat_enc(sh[q].mb));
     }
-    return t;
+    return StatAcc{h, stat_dec(mv), stat_dec(mn), stat_dec(mb)};
 }
 
 // r_i from a finished dot; writes c_i and folds the row into the stats.
@@ -239,7 +285,9 @@ __device__ __forceinline__ bool last_block(DevState *st, int nblk, int *sh_last)
     return true;
 }
 
-template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_row_kernel(const SparseArgs p)
+// At most 48 registers (five 256-thread CTAs per SM): the row pass is bound
+// by its gathers, so the loads in flight per SM set its speed.
+template <typename T, int W> __global__ void __launch_bounds__(kThreads, 5) sparse_row_kernel(const SparseArgs p)
 {
     using Meta = typename SpTraits<T>::Meta;
     DevState *st = p.st;
@@ -299,15 +347,16 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
     }
     if (!last_block(st, nblk, &sh_last))
         return;
-    StatAcc u{0, -INFINITY, -INFINITY, 0.0};
+    long long uh = 0;
+    unsigned long long umv = stat_enc(-INFINITY), umn = umv, umb = stat_enc(0.0);
     for (int q = threadIdx.x; q < nblk; q += kThreads) {
         const PartStat *ps = p.part_stat + q;
-        u.h += __ldcg(&ps->h);
-        u.mv = fmax(u.mv, __ldcg(&ps->maxviol));
-        u.mn = fmax(u.mn, __ldcg(&ps->maxnorm));
-        u.mb = fmax(u.mb, __ldcg(&ps->maxb));
+        uh += __ldcg(&ps->h);
+        umv = max(umv, stat_enc(__ldcg(&ps->maxviol)));
+        umn = max(umn, stat_enc(__ldcg(&ps->maxnorm)));
+        umb = max(umb, stat_enc(__ldcg(&ps->maxb)));
     }
-    const StatAcc tot = block_stats(u, sh_stat);
+    const StatAcc tot = block_stats(StatAcc{uh, stat_dec(umv), stat_dec(umn), stat_dec(umb)}, sh_stat);
     if (threadIdx.x == 0) {
         decide(st, tot, p.mode);
         st->ticket = 0u;
@@ -347,7 +396,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
     const T *coef = static_cast<const T *>(p.coef);
     const long long h = st->h;
     const int rule = st->rule;
-    const double s_relaxed = h > 0 ? st->lambda / (double)h : 0.0;
+    const double s_relaxed = h > 0 ? (p.rtab ? __ldg(p.rtab + h) : st->lambda / (double)h) : 0.0;
     const int nblk = p.n_col_pieces + p.col_light_ctas;
     double part = 0.0;
 
