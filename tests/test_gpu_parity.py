@@ -98,11 +98,9 @@ def test_map_reduce_one_step(storage, m, n):
 @pytest.mark.parametrize("n", [3000, 12000])
 @pytest.mark.parametrize("big", [40000.0, 2.0 ** 33])
 def test_fp8_large_x_and_slice_coefficients(n, big):
-    """FP8 decodes the odd element of each pair scaled by 2^-112 and carries
-    2^112 in its partner factor, except where that factor would not be
-    finite: a thread with an odd x entry of magnitude >= 2^15, a row with a
-    slice coefficient >= 2^15.  x entries of 40000 send some threads down
-    the plain decode; 2^33 also sends rows there.  Parity as everywhere."""
+    """FP8 storage with a few x entries far outside the typical range (40000
+    and 2^33, at odd and even columns): residuals and slice coefficients of
+    very different magnitudes in one Map.  Parity as everywhere."""
     m = 1500
     p = workloads.dense_system(m, n, seed=31 + n)
     x = p["x0"].copy()
@@ -431,3 +429,36 @@ def test_long_rows_one_step_and_trajectory(storage, m, n):
             s.iterate(1, rho=1e-3)
             xg = s.get_x()
             assert np.linalg.norm(xg - x) <= tol * np.linalg.norm(x), k
+
+
+# ------------------------------------------------------------------ step-size table
+
+@pytest.mark.parametrize("kind", ["dense-f64", "dense-f32", "sparse-f64-grid"])
+def test_step_size_changes_between_runs(monkeypatch, kind):
+    """The relaxed step reads lambda / h from a table filled when a run
+    begins with a new lambda: alternating lambda on one handle must give the
+    oracle's step every time (one step from the device's own x_k; rows within
+    rounding of zero would make the step ambiguous, and the seeds avoid them)."""
+    monkeypatch.setenv("NSLI_SPARSE_RESIDENT", "0")
+    if kind.startswith("dense"):
+        storage = kind.split("-")[1]
+        p = workloads.dense_system(700, 300, seed=61)
+        A = p["A"].astype(np.float64) if storage == "f64" else stored_values(p["A"], storage)
+        src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
+        make = lambda: nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage)
+    else:
+        storage = "f64"
+        p = workloads.sparse_system(700, 300, 8, seed=62)
+        A = workloads.csr_to_dense(p["rp"], p["ci"], p["val"], p["n"])
+        make = lambda: nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"],
+                                         Av=p["Av"], storage="f64")
+    n2, _ = oracle.norms2(A)
+    tol = 1e-12 if storage == "f64" else 1e-5
+    with make() as s:
+        for k, lam in enumerate([1.0, 0.5, 0.5, 1.7, 1.0]):
+            xk = s.get_x()
+            code, x_ref, st, y, r = oracle.iteration(A, p["b0"], p["Av"], 0.0, k, n2, xk, lam=lam,
+                                                     rule=oracle.RULE_RELAXED)
+            s.iterate(1, lam=lam, rule="relaxed", rho=0.0)
+            x1 = s.get_x()
+            assert np.linalg.norm(x1 - x_ref) / np.linalg.norm(x_ref) <= tol, (k, lam)
