@@ -571,22 +571,23 @@ template <typename T> __global__ void sparse_rows_kernel(const SparseArgs p, lon
 
 // ---- small systems: a whole block of iterations in one CTA --------------------
 //
-// When the binary64 iterate, y, and x and the coefficients c in the
-// accumulation type fit in one CTA's shared memory, one CTA on one SM runs up
-// to `iters` iterations per launch: an iteration costs a few block barriers
-// instead of two or three launches and their grid-wide hand-offs.  The steps
-// and decisions are those of the grid kernels above, in an order of their
-// own: rows one per thread in CSR order (rows longer than kResLong by one
-// warp each: lane-strided partial sums, then a butterfly); the row counts and
+// When the binary64 iterate, y, x and the coefficients c in the
+// accumulation type, and a table of lambda / h fit in one CTA's shared
+// memory, one CTA on one SM runs up to `iters` iterations per launch: an
+// iteration costs a few block barriers instead of two or three launches and
+// their grid-wide hand-offs.  The steps and decisions are those of the grid
+// kernels above, in an order of their own: short rows one per thread in CSR
+// order, two rows at a time (rows longer than kResLong on warps of their
+// own: lane-strided running sums, a tree, a butterfly); the row counts and
 // maxima folded exactly (integers and order-preserving encodings); the stop
-// decision taken by every thread from the same totals; columns one per
-// thread in CSC order (long ones by warps), each giving the relaxed step of
-// its x_j, or ModAP's y_j followed by ||y|| and the step; the sum of dx^2 (of
-// y^2) folded in a fixed order.  Only x, x64 and DevState persist between
-// launches (global memory), so launches of any size give identical results.
-// The statistics a stop rule does not read are not formed: DevState keeps
-// h and max r_i always, max r_i / ||a_i|| only under EPSMEM and max |b_i|
-// only under MAXVIOL_REL (-inf / 0 otherwise).
+// decision by thread 0 while the other threads gather y_j in CSC order over
+// the violated rows (long columns by warps); the relaxed step, or ||y|| and
+// ModAP's step; the terms of ||dx|| after the step's barrier, folded in a
+// fixed order.  Only x, x64 and DevState persist between launches (global
+// memory), so launches of any size give identical results.  The statistics
+// a stop rule does not read are not formed: DevState keeps h and max r_i
+// always, max r_i / ||a_i|| only under EPSMEM and max |b_i| only under
+// MAXVIOL_REL (-inf / 0 otherwise).
 
 __device__ __forceinline__ double sp_ord_dec(unsigned long long u)
 {
