@@ -680,7 +680,14 @@ EpiArgs epi_args(nsli_batch h, int mode)
 cudaError_t launch_gemm(nsli_batch h, int mode)
 {
     const EpiArgs e = epi_args(h, mode == 0 ? 0 : 3);
-    const int grid = std::min(h->num_sms, e.nwork);
+    // the fewest CTAs that take the work items in as many rounds as one CTA
+    // per SM would (512 row tiles on 152 SMs: 128 CTAs of 4 tiles each, the
+    // same rounds with less contention); NSLI_BATCH_GRID=sms keeps one per SM
+    const int rounds = (e.nwork + h->num_sms - 1) / h->num_sms;
+    int grid = (e.nwork + rounds - 1) / rounds;
+    if (const char *env = std::getenv("NSLI_BATCH_GRID"))
+        if (std::strcmp(env, "sms") == 0)
+            grid = std::min(h->num_sms, e.nwork);
     if (mode == 0) {
         gemm_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(h->tmA, h->tmX, e);
         return cudaGetLastError();
