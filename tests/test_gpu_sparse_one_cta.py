@@ -167,3 +167,25 @@ def test_iteration_cap_and_model_system_x(monkeypatch):
     assert res["status"] == nsli.OK
     assert abs(res["iters"] - ref["iters"]) <= max(1, 0.01 * ref["iters"])
     np.testing.assert_allclose(xg, ref["x"], rtol=0, atol=1e-6 * np.abs(p["b0"]).max())
+
+
+def test_shared_memory_limit(monkeypatch):
+    """The largest binary32 system whose x64, y, x, c and step table fit the
+    one-CTA shared-memory limit (8000 x 6000: 216008 of 221184 bytes) runs on
+    one CTA and matches the oracle's step; 300 more columns (222008 bytes)
+    fall back to the grid kernels even when the one-CTA path is forced."""
+    p = workloads.sparse_system(8000, 6000, 4, seed=17)
+    with make(monkeypatch, p, "f32") as s:
+        assert launches_for(s, 4, 4) == 1 + 1
+    with make(monkeypatch, p, "f32") as s:
+        s.iterate(2, rule="relaxed", lam=1.0, rho=1e-3)
+        xk = s.get_x()
+        ref = one_step_check(s, p, "f32", xk, 2, 1e-3, "relaxed", 1.0)
+        if ref is False:
+            pytest.skip("a row of this seeded case is within rounding of its bound")
+        s.iterate(1, rule="relaxed", lam=1.0, rho=1e-3)
+        x1 = s.get_x()
+    assert np.linalg.norm(x1 - ref) / np.linalg.norm(ref) <= 1e-5
+    wider = workloads.sparse_system(8000, 6300, 4, seed=18)
+    with make(monkeypatch, wider, "f32") as s:
+        assert launches_for(s, 4, 4) == 1 + 2 * 4
