@@ -654,6 +654,28 @@ __device__ __forceinline__ long long abs_bits(double v) { return __double_as_lon
 // ends the step, their sum only when the step rule can hold (and for the
 // last step of a launch).
 
+// acc + a * v where acc is still the exact zero it started as: for a = +1 or
+// -1 (bound rows and columns) the product is v or -v exactly and no binary64
+// operation is needed; the coefficient is recognised from its bit pattern.
+__device__ __forceinline__ double first_term(double a, double v)
+{
+    const long long b = __double_as_longlong(a);
+    if (b == 0x3ff0000000000000ll)
+        return v;
+    if (b == (long long)0xbff0000000000000ull)
+        return -v;
+    return a * v;
+}
+__device__ __forceinline__ float first_term(float a, float v)
+{
+    const int b = __float_as_int(a);
+    if (b == 0x3f800000)
+        return v;
+    if (b == (int)0xbf800000u)
+        return -v;
+    return a * v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const SparseArgs p, int iters)
 {
@@ -773,7 +795,11 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 const bool ok0 = b0 - a0 <= kResLong, ok1 = i1 < m && b1 - a1 <= kResLong;
                 const long long l0 = ok0 ? b0 - a0 : 0, l1 = ok1 ? b1 - a1 : 0;
                 T s0 = T(0), s1 = T(0);
-                for (long long q = 0; q < max(l0, l1); ++q) {
+                if (l0 > 0)
+                    s0 = first_term(__ldg(va + a0), xs[__ldg(p.ci + a0)]);
+                if (l1 > 0)
+                    s1 = first_term(__ldg(va + a1), xs[__ldg(p.ci + a1)]);
+                for (long long q = 1; q < max(l0, l1); ++q) {
                     if (q < l0)
                         s0 = fma(__ldg(va + a0 + q), xs[__ldg(p.ci + a0 + q)], s0);
                     if (q < l1)
@@ -868,10 +894,13 @@ __global__ void __launch_bounds__(kResThreads, 1) sparse_resident_kernel(const S
                 if (e1 - e0 > kResLong)
                     continue;
                 T y = T(0);
+                bool first = true;
                 for (long long e = e0; e < e1; ++e) {
                     const T c = cs[__ldg(p.ri + e)];
-                    if (c != T(0))
-                        y = fma(__ldg(vc + e), c, y);
+                    if (c != T(0)) {
+                        y = first ? first_term(__ldg(vc + e), c) : fma(__ldg(vc + e), c, y);
+                        first = false;
+                    }
                 }
                 ys[j] = (double)y;
             }
