@@ -30,7 +30,7 @@
 //
 // Small systems (x, y, the coefficients and a lambda / h table fit one CTA's
 // shared memory, the matrix its L1) run instead on sparse_resident_kernel:
-// one CTA, a whole block of iterations per launch (at the end of this file).
+// one CTA, a whole block of iterations per launch (further below).
 #include <cstdint>
 
 #include "nsli.h"
