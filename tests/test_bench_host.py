@@ -36,7 +36,7 @@ def test_traffic_record_matches_the_map_source(storage):
 
 def test_map_source_hash_covers_the_map_kernel():
     """The hashed prefix (up to the long-row section) holds the Map kernel's
-    body and its launcher; the long-row kernel lies after it."""
+    body and its kernels; the long-row kernel lies after it."""
     src = open(os.path.join(ROOT, "paper_2003_09956_gb300", "csrc", "nsli_kernels.cu")).read()
     end = src.find(bench.MAP_SOURCE_END)
     assert end > 0
