@@ -17,6 +17,8 @@ Non-stationary Systems of Linear Inequalities" (2020).
   - eps-membership stopping test: Eq. 10
   - ModAP fixed-length step psi = lambda * y / ||y||: Eq. 12
   - Map / Reduce list form: Eq. 13 and the ModAP-on-lists description (Section 3)
+  - ModAPL's split of the list among workers and the global Reduce of their
+    partial results (Section 3): combine_step
 
 Every function here is pinned by the ``-m "not gpu"`` tests against closed
 forms, brute force on small systems, invariants and library routines.
@@ -105,6 +107,9 @@ def _load():
         lib.oracle_solve.argtypes = [i64, i64, P, P, P, dbl, i64, P, P, dbl, ip,
                                      ip, dbl, i64, P, P]
         lib.oracle_solve.restype = None
+        lib.oracle_combine_step.argtypes = [i64, i64, P, P, P, P, P, P, dbl, ip, ip, dbl, ip,
+                                            P, P]
+        lib.oracle_combine_step.restype = ip
         lib.oracle_map_reduce_f32.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_map_reduce_f32.restype = None
         lib.oracle_norms2_f32.argtypes = [i64, i64, P, P]
@@ -221,6 +226,32 @@ def iteration(A, b0, Av, rho, k, n2, x, lam=1.0, rule=RULE_RELAXED,
     st = {"h": int(stats[0]), "maxviol": stats[1], "maxnorm": stats[2],
           "maxb": stats[3], "dx_norm": stats[4], "y_norm": stats[5]}
     return int(code), x, st, y, r
+
+
+def combine_step(records, x, lam=1.0, rule=RULE_RELAXED, stop=STOP_NONE, eps=0.0,
+                 force_step=False):
+    """The exchange of ModAPL (Section 3): the per-worker Map/Reduce outputs
+    ``records`` (a list, in worker order, of dicts with y, h, maxviol,
+    maxnorm, maxb as map_reduce returns them) are combined in worker order,
+    then the decision and step of one iteration are taken at x.
+    Returns (code, x_new, stats, y)."""
+    R = len(records)
+    x = np.array(x, dtype=np.float64, copy=True)
+    n = x.shape[0]
+    ys = np.ascontiguousarray(np.stack([_f64(r["y"]) for r in records]) if R else
+                              np.zeros((0, n)))
+    hs = np.ascontiguousarray([int(r["h"]) for r in records], dtype=np.int64)
+    mvs = _f64([r["maxviol"] for r in records])
+    mns = _f64([r["maxnorm"] for r in records])
+    mbs = _f64([r["maxb"] for r in records])
+    y = np.empty(n, np.float64)
+    stats = np.zeros(6, np.float64)
+    code = _load().oracle_combine_step(R, n, _ptr(ys), _ptr(hs), _ptr(mvs), _ptr(mns), _ptr(mbs),
+                                       _ptr(x), float(lam), int(rule), int(stop), float(eps),
+                                       int(bool(force_step)), _ptr(y), _ptr(stats))
+    st = {"h": int(stats[0]), "maxviol": stats[1], "maxnorm": stats[2],
+          "maxb": stats[3], "dx_norm": stats[4], "y_norm": stats[5]}
+    return int(code), x, st, y
 
 
 def solve(A, b0, x0, Av=None, rho=0.0, k0=0, n2=None, lam=1.0,

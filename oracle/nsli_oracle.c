@@ -264,6 +264,53 @@ static int stop_test_passes(int stop, double eps, double maxviol,
     return 0;
 }
 
+/* The decision and the step of one iteration, given the Reduce's outputs at
+ * (x_k, b(k)): the top-of-iteration test (Eq. 10 or max r_i <= eps max|b|,
+ * h == 0 meaning x in M), then the relaxed step x <- x - lambda y / h
+ * (Eq. 8) or the fixed-length step x <- x - lambda y / ||y|| (Eq. 12).
+ * x[n] is updated in place when a step is taken; stats as for
+ * oracle_iteration (stats[0..3] already hold h and the maxima). */
+static int decide_and_step(int64_t n, double *x, const double *y, int64_t h,
+                           double maxviol, double maxnorm, double maxb,
+                           double lambda, int rule, int stop, double eps,
+                           int force_step, double *stats)
+{
+    stats[4] = 0.0;
+    stats[5] = 0.0;
+
+    double ynorm2 = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        ynorm2 = ynorm2 + y[j] * y[j];
+    double ynorm = sqrt(ynorm2);
+    stats[5] = ynorm;
+
+    if (!force_step) {
+        if (stop != ORACLE_STOP_NONE && h == 0)
+            return ORACLE_IT_CONVERGED; /* x lies in M(t): phi = 0 */
+        if (stop_test_passes(stop, eps, maxviol, maxnorm, maxb))
+            return ORACLE_IT_CONVERGED;
+    }
+
+    /* step: relaxed Eq. 8 or fixed-length Eq. 12 */
+    double dx2 = 0.0;
+    if (h > 0) {
+        double s;
+        if (rule == ORACLE_RULE_MODAP)
+            s = (ynorm > 0.0) ? lambda / ynorm : 0.0;
+        else
+            s = lambda / (double)h;
+        for (int64_t j = 0; j < n; ++j) {
+            double d = s * y[j];
+            x[j] = x[j] - d;
+            dx2 = dx2 + d * d;
+        }
+    }
+    stats[4] = sqrt(dx2);
+    if (stop == ORACLE_STOP_STEP && stats[4] < eps)
+        return ORACLE_IT_STEP_STOP;
+    return ORACLE_IT_STEPPED;
+}
+
 /* One iteration of Algorithm 1 / ModAP at tick k (the order of the ModAP-on-
  * lists description in Section 3: Map, Reduce, step, data update, test; the
  * test of step k+1 is evaluated here at the top of iteration k+1).
@@ -287,40 +334,48 @@ int oracle_iteration(int64_t m, int64_t n, const double *A, const double *b0,
     stats[1] = maxviol;
     stats[2] = maxnorm;
     stats[3] = maxb;
-    stats[4] = 0.0;
-    stats[5] = 0.0;
+    return decide_and_step(n, x, work, h, maxviol, maxnorm, maxb, lambda, rule,
+                           stop, eps, force_step, stats);
+}
 
-    double ynorm2 = 0.0;
+/* The exchange of ModAPL (Section 3, the list form split into sublists, one
+ * per worker): worker w = 0..R-1 has run the Map and a local Reduce over its
+ * own contiguous block of rows at (x_k, b(k)) and produced (y_w, h_w, and its
+ * maxima).  The global Reduce adds the y_w in worker order w = 0, 1, ...,
+ * R-1 (sequentially, element by element), adds the h_w and takes the maxima;
+ * then the decision and the step are those of oracle_iteration.  ys holds
+ * the R vectors y_w row-major (R x n); hs, maxviols, maxnorms, maxbs hold R
+ * values each.  x[n] is updated in place; y_out[n] receives the global y;
+ * stats as for oracle_iteration.  Returns one of ORACLE_IT_*. */
+int oracle_combine_step(int64_t R, int64_t n, const double *ys,
+                        const int64_t *hs, const double *maxviols,
+                        const double *maxnorms, const double *maxbs,
+                        double *x, double lambda, int rule, int stop,
+                        double eps, int force_step, double *y_out,
+                        double *stats)
+{
+    int64_t h = 0;
+    double mv = -INFINITY, mn = -INFINITY, mb = 0.0;
     for (int64_t j = 0; j < n; ++j)
-        ynorm2 = ynorm2 + work[j] * work[j];
-    double ynorm = sqrt(ynorm2);
-    stats[5] = ynorm;
-
-    if (!force_step) {
-        if (stop != ORACLE_STOP_NONE && h == 0)
-            return ORACLE_IT_CONVERGED; /* x lies in M(t): phi = 0 */
-        if (stop_test_passes(stop, eps, maxviol, maxnorm, maxb))
-            return ORACLE_IT_CONVERGED;
+        y_out[j] = 0.0;
+    for (int64_t w = 0; w < R; ++w) {
+        const double *yw = ys + w * n;
+        for (int64_t j = 0; j < n; ++j)
+            y_out[j] = y_out[j] + yw[j];
+        h = h + hs[w];
+        if (maxviols[w] > mv)
+            mv = maxviols[w];
+        if (maxnorms[w] > mn)
+            mn = maxnorms[w];
+        if (maxbs[w] > mb)
+            mb = maxbs[w];
     }
-
-    /* step: relaxed Eq. 8 or fixed-length Eq. 12 */
-    double dx2 = 0.0;
-    if (h > 0) {
-        double s;
-        if (rule == ORACLE_RULE_MODAP)
-            s = (ynorm > 0.0) ? lambda / ynorm : 0.0;
-        else
-            s = lambda / (double)h;
-        for (int64_t j = 0; j < n; ++j) {
-            double d = s * work[j];
-            x[j] = x[j] - d;
-            dx2 = dx2 + d * d;
-        }
-    }
-    stats[4] = sqrt(dx2);
-    if (stop == ORACLE_STOP_STEP && stats[4] < eps)
-        return ORACLE_IT_STEP_STOP;
-    return ORACLE_IT_STEPPED;
+    stats[0] = (double)h;
+    stats[1] = mv;
+    stats[2] = mn;
+    stats[3] = mb;
+    return decide_and_step(n, x, y_out, h, mv, mn, mb, lambda, rule, stop, eps,
+                           force_step, stats);
 }
 
 /* The whole iterative process: iterations at ticks k0, k0+1, ... until the

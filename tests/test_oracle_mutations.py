@@ -27,6 +27,9 @@ MUTATIONS = [
     ("bf16 rounds half up", "u = u + 0x7fffu + keep_lsb;", "u = u + 0x8000u;"),
     ("e4m3 scale target 480", "while (ldexp(amax, -e) > 448.0)", "while (ldexp(amax, -e) > 480.0)"),
     ("e4m3 subnormal quantum", "quantum = ldexp(1.0, -9); /* subnormal spacing */", "quantum = ldexp(1.0, -8);"),
+    ("exchange takes h as a maximum", "h = h + hs[w];", "h = (hs[w] > h) ? hs[w] : h;"),
+    ("exchange drops worker 0's y", "y_out[j] = y_out[j] + yw[j];", "y_out[j] = (w > 0) ? y_out[j] + yw[j] : 0.0;"),
+    ("exchange keeps the first worker's maximum", "if (maxviols[w] > mv)", "if (w == 0 && maxviols[w] > mv)"),
 ]
 
 PIN_CALLS = [
@@ -46,6 +49,9 @@ PIN_CALLS = [
     pins.test_norms_match_library,
     pins.test_bf16_rounding_matches_library_bit_exact,
     pins.test_e4m3_rounding_matches_library_bit_exact,
+    lambda: pins.test_combine_hand_worked_2d_split_over_workers([(0, 1), (1, 3)]),
+    lambda: pins.test_combine_hand_worked_2d_split_over_workers([(0, 2), (2, 3)]),
+    lambda: pins.test_combine_hand_worked_2d_split_over_workers([(0, 0), (0, 3)]),
 ]
 
 

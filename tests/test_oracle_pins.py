@@ -445,3 +445,93 @@ def test_csr_model_system_is_the_model_system():
     n2, zero = oracle.norms2_csr(p["rp"], p["val"])
     np.testing.assert_array_equal(n2, np.r_[np.ones(14), 7.0])
     assert zero == 0
+
+
+# ------------------------------------------------------------------ ModAPL exchange
+
+def _split_records(A, b, n2, x, bounds):
+    """Each worker's Map and local Reduce over its contiguous block of rows."""
+    return [oracle.map_reduce(np.ascontiguousarray(A[a:c]), b[a:c], n2[a:c], x) for a, c in bounds]
+
+
+@pytest.mark.parametrize("bounds", [[(0, 1), (1, 3)], [(0, 2), (2, 3)], [(0, 1), (1, 2), (2, 3)],
+                                    [(0, 0), (0, 3)]])
+def test_combine_hand_worked_2d_split_over_workers(bounds):
+    """The hand-worked 2-D example (tests/golden/hand_worked_2d.txt) with its
+    rows split among workers: the global Reduce of ModAPL (Section 3) gives
+    the worked y, h, maxima and both steps, whatever the split."""
+    g = load_golden("hand_worked_2d.txt")
+    A = np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, -1.0]])
+    b = np.array([1.0, 1.0, 10.0])
+    n2 = np.array([1.0, 1.0, 2.0])
+    x0 = np.array(g["case1.x0"])
+    recs = _split_records(A, b, n2, x0, bounds)
+    code, x1, st, y = oracle.combine_step(recs, x0, lam=1.0, rule=oracle.RULE_RELAXED)
+    assert code == oracle.IT_STEPPED
+    np.testing.assert_array_equal(y, g["case1.y"])
+    assert st["h"] == g["case1.h"][0]
+    assert st["maxviol"] == g["case1.maxviol"][0] and st["maxnorm"] == g["case1.maxnorm"][0]
+    np.testing.assert_array_equal(x1, g["case1.relaxed_x1"])
+    _, x1m, _, _ = oracle.combine_step(recs, x0, lam=1.0, rule=oracle.RULE_MODAP)
+    np.testing.assert_allclose(x1m, g["case1.modap_x1"], rtol=0, atol=1e-15)
+
+
+def test_combine_one_worker_equals_iteration():
+    """One worker holding every row: the combined step is oracle.iteration's
+    step bit for bit (same arithmetic in the same order)."""
+    p = workloads.dense_system(400, 37, seed=71)
+    A = p["A"].astype(np.float64)
+    n2, _ = oracle.norms2(A)
+    for rule in (oracle.RULE_RELAXED, oracle.RULE_MODAP):
+        code, x1, st, y, _ = oracle.iteration(A, p["b0"], p["Av"], 1e-2, 3, n2, p["x0"], lam=0.7, rule=rule)
+        b = oracle.tick_b(p["b0"], p["Av"], 1e-2, 3)
+        c2, x2, st2, y2 = oracle.combine_step(_split_records(A, b, n2, p["x0"], [(0, 400)]), p["x0"],
+                                              lam=0.7, rule=rule)
+        assert c2 == code
+        np.testing.assert_array_equal(x2, x1)
+        np.testing.assert_array_equal(y2, y)
+        assert st2 == st
+
+
+@pytest.mark.parametrize("R", [2, 3, 7])
+def test_combine_contiguous_splits_match_unsplit(R):
+    """R workers over contiguous balanced row blocks: h and the maxima are
+    exact, y and the step equal the unsplit ones to rounding (only the order
+    of the sums differs)."""
+    p = workloads.dense_system(501, 40, seed=72 + R)
+    A = p["A"].astype(np.float64)
+    n2, _ = oracle.norms2(A)
+    m = A.shape[0]
+    edges = [m * w // R for w in range(R + 1)]
+    bounds = list(zip(edges[:-1], edges[1:]))
+    full = oracle.map_reduce(A, p["b0"], n2, p["x0"])
+    recs = _split_records(A, p["b0"], n2, p["x0"], bounds)
+    code, x1, st, y = oracle.combine_step(recs, p["x0"])
+    assert st["h"] == full["h"] and st["maxviol"] == full["maxviol"]
+    assert st["maxnorm"] == full["maxnorm"] and st["maxb"] == full["maxb"]
+    np.testing.assert_allclose(y, full["y"], rtol=1e-13, atol=1e-13 * np.abs(full["y"]).max())
+    # reversed worker order: the same up to rounding
+    _, xr, str_, yr = oracle.combine_step(recs[::-1], p["x0"])
+    np.testing.assert_allclose(xr, x1, rtol=1e-13)
+    assert str_["h"] == st["h"]
+
+
+def test_combine_decisions_follow_the_stop_rules():
+    """The stop decision after the exchange: all workers feasible (h = 0)
+    stops under any rule but NONE; max r <= eps max|b| over ALL workers."""
+    A = np.array([[1.0, 0.0], [0.0, 1.0]])
+    n2 = np.ones(2)
+    x = np.array([0.5, 2.0])
+    b = np.array([1.0, 1.0])
+    recs = _split_records(A, b, n2, x, [(0, 1), (1, 2)])
+    assert recs[0]["h"] == 0 and recs[1]["h"] == 1
+    code, x1, _, _ = oracle.combine_step(recs, x, stop=oracle.STOP_MAXVIOL_REL, eps=0.5)
+    assert code == oracle.IT_STEPPED                  # max r = 1 > 0.5 * max|b| = 0.5
+    np.testing.assert_array_equal(x1, [0.5, 1.0])
+    code, x2, _, _ = oracle.combine_step(recs, x, stop=oracle.STOP_MAXVIOL_REL, eps=1.0)
+    assert code == oracle.IT_CONVERGED
+    np.testing.assert_array_equal(x2, x)
+    feas = _split_records(A, b, n2, np.array([0.5, 0.5]), [(0, 1), (1, 2)])
+    assert oracle.combine_step(feas, np.array([0.5, 0.5]), stop=oracle.STOP_STEP, eps=1e-9)[0] == \
+        oracle.IT_CONVERGED
+    assert oracle.combine_step(feas, np.array([0.5, 0.5]), stop=oracle.STOP_NONE)[0] == oracle.IT_STEPPED
