@@ -10,11 +10,11 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2003_09956_gb300 import nsli, workloads
 
 pytestmark = pytest.mark.gpu
 
-U = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24, "fp8": 2.0 ** -24}
 STORAGES = ["f64", "f32", "bf16", "fp8"]
 
 
@@ -23,6 +23,11 @@ def built_library():
     from paper_2003_09956_gb300 import _build
     _build.build()
     nsli.load()
+
+
+def num_sms():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def stored_values(A32, storage):
@@ -36,41 +41,32 @@ def stored_values(A32, storage):
 
 
 def ambiguity_bound(A, x, b, u):
-    """|computed r_i - exact r_i| <= bound_i for the kernel's accumulation
-    (per-thread sequential partial sums of at most 32 products, a 5-level
-    warp tree and a <= 16-term block sum): gamma_k * (sum |a_ij x_j| + |b_i|)
-    with k = 64 levels and a factor 4 of slack."""
-    Ad = np.asarray(A, np.float64)
-    return 4.0 * 64 * u * (np.abs(Ad) @ np.abs(x) + np.abs(b) + 1e-300)
+    """Rigorous bound on the accumulation type's error in r_i (64 levels)."""
+    return parity.residual_bound(A, x, b, u, levels=64)
 
 
-def check_map_reduce(solver, A_eff, b, x, storage, tol_rel=1e-5):
+def check_map_reduce(solver, A_eff, b, x, storage):
+    """One Map/Reduce through the C ABI against the oracle, element by
+    element (tests/parity.py)."""
     y_g, h_g, st_g = solver.map_reduce()
-    n2, _ = oracle.norms2(A_eff)
-    mr = oracle.map_reduce(A_eff, b, n2, x)
-    r = mr["r"]
-    bound = ambiguity_bound(A_eff, x, b, U[storage])
-    amb = np.abs(r) <= bound
-    sure = (r > 0) & ~amb
-    h_sure = int(sure.sum())
-    assert h_sure <= h_g <= h_sure + int(amb.sum()), (h_g, h_sure, int(amb.sum()))
-    # oracle sum over the rows whose classification is fixed
-    keep = ~amb
-    if keep.all():
-        y_ref = mr["y"]
-    else:
-        y_ref = oracle.map_reduce(np.ascontiguousarray(A_eff[keep]), b[keep], n2[keep], x)["y"]
-    slack = float(np.sum(bound[amb] / np.sqrt(n2[amb]))) if amb.any() else 0.0
-    # each violated row's slice carries a rounding error bounded like its residual
-    slack += float(np.sum(bound[sure] / np.sqrt(n2[sure])))
-    err = np.linalg.norm(y_g - y_ref)
-    scale = np.linalg.norm(y_ref)
-    assert err <= tol_rel * scale + slack, (err, scale, slack)
-    # maxima (the kernel works in its accumulation type)
-    tol_m = 4 * float(bound.max()) + 1e-12
-    assert abs(st_g["maxviol"] - mr["maxviol"]) <= tol_m
-    assert abs(st_g["maxb"] - mr["maxb"]) <= 1e-6 * max(1.0, mr["maxb"])
-    return mr, h_g
+    m, n = A_eff.shape
+    ref = parity.check_map_reduce(y_g, h_g, st_g, A_eff, b, x, storage,
+                                  depth=parity.dense_y_depth(m, num_sms()),
+                                  levels=parity.dot_levels(n))
+    return ref.mr, h_g
+
+
+def step_and_check(solver, A_eff, b_k, storage, lam=1.0, rule="relaxed", rho=0.0, n2=None):
+    """One iteration on the device from its own x_k, checked element by
+    element against the oracle's step from the same point."""
+    xk = solver.get_x()
+    solver.iterate(1, lam=lam, rule=rule, rho=rho)
+    x1 = solver.get_x()
+    m, n = A_eff.shape
+    parity.check_step(xk, x1, solver.result()["h"], A_eff, b_k, storage,
+                      depth=parity.dense_y_depth(m, num_sms()), lam=lam, rule=rule, n2=n2,
+                      levels=parity.dot_levels(n))
+    return xk, x1
 
 
 # ------------------------------------------------------------------ Map/Reduce
@@ -145,37 +141,40 @@ def oracle_trajectory(A_eff, p, rule, lam, rho, K):
 @pytest.mark.parametrize("rule", ["relaxed", "modap"])
 @pytest.mark.parametrize("rho", [0.0, 1e-3])
 def test_trajectory_matches_oracle(storage, rule, rho):
-    """Iterates agree to 1e-5 relative (1e-12 for binary64 storage) at every
-    iteration, compared until the first Map with an ambiguous row: one whose
-    oracle residual is within the rounding bound plus ||a_i|| times the
-    current distance between the two iterates (from then on both
-    classifications, hence both trajectories, are correct)."""
-    m, n, K = 800, 257, 15
+    """Every iteration's step, taken on the device from its own x_k, equals
+    the oracle's step from that x_k element by element (tests/parity.py:
+    1e-5 relative per element, 1e-12 for binary64 storage, plus the column's
+    rounding bound), over 30 iterations.  The two independent trajectories
+    also agree to the same tolerance relative to ||x|| until the first Map
+    with an ambiguous row (one whose oracle residual is within the rounding
+    bound plus ||a_i|| times the distance between the two iterates: from
+    then on both classifications, hence both trajectories, are correct)."""
+    m, n, K = 800, 257, 30
     p = workloads.dense_system(m, n, seed=5 + int(rho * 1e4))
     A_eff = stored_values(p["A"], storage)
     src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
     lam = 1.0 if rule == "relaxed" else 0.5
     orule = oracle.RULE_RELAXED if rule == "relaxed" else oracle.RULE_MODAP
-    tol = 1e-5 if storage != "f64" else 1e-12
+    tol = parity.TOL[storage]
     xs, rs, n2 = oracle_trajectory(A_eff, p, orule, lam, rho, K)
     compared = 0
+    together = True
     with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
         xg = s.get_x()
         for k in range(K):
-            drift = np.linalg.norm(xg - xs[k])
             b_k = oracle.tick_b(p["b0"], p["Av"], rho, k)
-            bound = ambiguity_bound(A_eff, xs[k], b_k, U[storage]) / 4 + \
-                np.sqrt(n2) * drift * 1.01
-            if np.any(np.abs(rs[k]) <= bound):
-                break
-            s.iterate(1, lam=lam, rule=rule, rho=rho)
-            xg = s.get_x()
-            rel = np.linalg.norm(xg - xs[k + 1]) / np.linalg.norm(xs[k + 1])
-            assert rel <= tol, (k, rel)
-            compared += 1
+            if together:
+                drift = np.linalg.norm(xg - xs[k])
+                bound = ambiguity_bound(A_eff, xs[k], b_k, parity.U[storage]) / 4 + \
+                    np.sqrt(n2) * drift * 1.01
+                together = not np.any(np.abs(rs[k]) <= bound)
+            _, xg = step_and_check(s, A_eff, b_k, storage, lam=lam, rule=rule, rho=rho, n2=n2)
+            if together:
+                rel = np.linalg.norm(xg - xs[k + 1]) / np.linalg.norm(xs[k + 1])
+                assert rel <= tol, (k, rel)
+                compared += 1
         assert compared >= 3, "seeded case became ambiguous too early"
-        res = s.result()
-        assert res["tick"] == compared
+        assert s.result()["tick"] == K
 
 
 def test_graph_blocks_equal_single_launches():
@@ -415,20 +414,16 @@ def test_long_rows_every_group_size(monkeypatch, budget_mb, storage, m, n):
 @pytest.mark.parametrize("storage,m,n", LONG)
 def test_long_rows_one_step_and_trajectory(storage, m, n):
     """Rows beyond the register-resident limit take the chunked two-pass
-    Map (violated rows re-read from L2); same parity bar."""
+    Map (violated rows re-read from L2); same parity bar, element by
+    element, for one Map/Reduce and three steps."""
     p = workloads.dense_system(m, n, seed=3000 + n)
     A_eff = stored_values(p["A"], storage)
     src = p["A"].astype(np.float64) if storage == "f64" else p["A"]
     with nsli.Solver(src, p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
         check_map_reduce(s, A_eff, p["b0"], p["x0"], storage)
         n2, _ = oracle.norms2(A_eff)
-        x = p["x0"].copy()
-        tol = 1e-5 if storage != "f64" else 1e-12
         for k in range(3):
-            _, x, _, _, _ = oracle.iteration(A_eff, p["b0"], p["Av"], 1e-3, k, n2, x)
-            s.iterate(1, rho=1e-3)
-            xg = s.get_x()
-            assert np.linalg.norm(xg - x) <= tol * np.linalg.norm(x), k
+            step_and_check(s, A_eff, oracle.tick_b(p["b0"], p["Av"], 1e-3, k), storage, rho=1e-3, n2=n2)
 
 
 # ------------------------------------------------------------------ step-size table
@@ -453,12 +448,11 @@ def test_step_size_changes_between_runs(monkeypatch, kind):
         make = lambda: nsli.SparseSolver(p["m"], p["n"], p["rp"], p["ci"], p["val"], p["b0"], p["x0"],
                                          Av=p["Av"], storage="f64")
     n2, _ = oracle.norms2(A)
-    tol = 1e-12 if storage == "f64" else 1e-5
     with make() as s:
         for k, lam in enumerate([1.0, 0.5, 0.5, 1.7, 1.0]):
             xk = s.get_x()
-            code, x_ref, st, y, r = oracle.iteration(A, p["b0"], p["Av"], 0.0, k, n2, xk, lam=lam,
-                                                     rule=oracle.RULE_RELAXED)
             s.iterate(1, lam=lam, rule="relaxed", rho=0.0)
             x1 = s.get_x()
-            assert np.linalg.norm(x1 - x_ref) / np.linalg.norm(x_ref) <= tol, (k, lam)
+            depth = parity.dense_y_depth(700, num_sms()) if kind.startswith("dense") else 700
+            parity.check_step(xk, x1, s.result()["h"], A, p["b0"], storage, depth=depth, lam=lam, n2=n2,
+                              levels=parity.dot_levels(300))
