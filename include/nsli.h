@@ -251,9 +251,10 @@ int nsli_get_result(nsli_handle h, nsli_result *out);
 
 /* Map + Reduce of a caller-held binary32 system that ALLOCATES NOTHING (the
  * paper has no counterpart; this is an interface for callers that cannot
- * allocate device memory: code running while a stream is captured into a
- * CUDA graph, and code under a fixed memory budget or a host framework's own
- * allocator).  With r_i = <a_i, x> - b_i it writes
+ * allocate device memory: code under a fixed device-memory budget, and code
+ * inside a host framework that owns all device memory through its own
+ * allocator and does not let libraries call cudaMalloc).  With
+ * r_i = <a_i, x> - b_i it writes
  *   y[j]       = sum over r_i > 0 of r_i / norms2[i] * a_ij   (n doubles),
  *   *violated  = #{i : r_i > 0},  *max_viol = max_i r_i  (binary32 sums).
  * Every pointer is a device pointer of the current device: A row-major, m
@@ -264,8 +265,10 @@ int nsli_get_result(nsli_handle h, nsli_result *out);
  * exits; n larger than 2^20 is rejected with NSLI_ERR_UNSUPPORTED.  The
  * first call on a device looks up that array's device address (once per
  * device), so make it before any stream capture.  All calls share the
- * array: calls that overlap on the GPU race and must not be issued.
- * Calls no cudaMalloc or cudaFree.  Returns NSLI_OK, NSLI_ERR_ARG,
+ * array and each call clears the part it accumulates into: calls that
+ * overlap on the GPU race and must not be issued.  Calls no cudaMalloc or
+ * cudaFree.  A CUDA error already pending when the call starts is left in
+ * place and nothing is launched.  Returns NSLI_OK, NSLI_ERR_ARG,
  * NSLI_ERR_UNSUPPORTED or NSLI_ERR_CUDA. */
 int nsli_map_reduce_noalloc(int64_t m, int64_t n, const float *A, int64_t lda,
                             const float *b, const float *norms2, const float *x,

@@ -1,14 +1,14 @@
 // nsli_noalloc.cu -- a Map + Reduce entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (an allocation there is an error or breaks the
-// capture), and code that runs under a fixed device-memory budget or behind
-// a host framework's own allocator, which forbids libraries from taking
-// device memory of their own.  nsli_map_reduce_noalloc serves them: the
-// caller passes every input and output, and the kernels' scratch (one row
-// of partial sums per CTA, and per-CTA counters) lives in the file-scope
-// array below, which every GPU that loads this library holds until the
-// process exits.
+// Some callers cannot call cudaMalloc: code that runs under a fixed
+// device-memory budget, and code inside a host framework that owns all
+// device memory through its own allocator and does not let libraries take
+// memory of their own (a cudaMalloc there can fail, or push the framework
+// past its budget; cudaFree also waits for the whole device).
+// nsli_map_reduce_noalloc serves them: the caller passes every input and
+// output, and the kernels' scratch (one row of partial sums per CTA, and
+// per-CTA counters) lives in the file-scope array below, which every GPU
+// that loads this library holds until the process exits.
 //
 // The array is shared by every call: calls that overlap on the GPU (for
 // example on two streams at once) race on it and must not be issued.  Each
@@ -161,6 +161,10 @@ extern "C" int nsli_map_reduce_noalloc(int64_t m, int64_t n, const float *A, int
     float *part = reinterpret_cast<float *>(ds->ptr);
     CtaStat *stat = reinterpret_cast<CtaStat *>(ds->ptr + kScratchFloats * 4);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // an error left pending by the caller's own work is not ours to report
+    // or to clear: leave it in place and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return NSLI_ERR_CUDA;
     noalloc_map_kernel<<<(unsigned int)G, kThreads, 0, s>>>(A, lda, m, n, b, norms2, x, part, stat, m / G,
                                                             (int)(m % G));
     if (cudaGetLastError() != cudaSuccess)

@@ -237,13 +237,37 @@ def _sync_torch_inputs(*arrays):
 
 
 def map_reduce_noalloc(A, b, norms2, x, y, violated, max_viol, stream=None):
-    """Allocation-free Map + Reduce on caller-held CUDA tensors (all float32
-    inputs, outputs y float64[n], violated int64[1], max_viol float64[1]).
-    For callers that cannot allocate device memory; see include/nsli.h."""
+    """Allocation-free Map + Reduce on caller-held CUDA tensors of one device:
+    A float32 (m, n) with unit column stride (row pitch A.stride(0) >= n),
+    b and norms2 float32[m], x float32[n]; outputs y float64[n], violated
+    int64[1], max_viol float64[1].  For callers that cannot allocate device
+    memory (see nsli_map_reduce_noalloc in include/nsli.h).  The work is
+    issued on ``stream`` (a cudaStream_t value), by default on torch's
+    current stream of A's device, and is not synchronised."""
+    import torch
+
+    if A.dim() != 2 or A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+        raise ValueError("A must be a 2-D tensor with rows of unit stride")
     m, n = int(A.shape[0]), int(A.shape[1])
-    rc = load().nsli_map_reduce_noalloc(m, n, _ptr(A), int(A.stride(0)), _ptr(b), _ptr(norms2),
-                                        _ptr(x), _ptr(y), _ptr(violated), _ptr(max_viol),
-                                        None if stream is None else ctypes.c_void_p(stream))
+    want = [("A", A, torch.float32, None), ("b", b, torch.float32, m),
+            ("norms2", norms2, torch.float32, m), ("x", x, torch.float32, n),
+            ("y", y, torch.float64, n), ("violated", violated, torch.int64, 1),
+            ("max_viol", max_viol, torch.float64, 1)]
+    for name, t, dt, numel in want:
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.device != A.device:
+            raise ValueError("%s is on %s, A on %s" % (name, t.device, A.device))
+        if t.dtype != dt:
+            raise ValueError("%s must be %s, got %s" % (name, dt, t.dtype))
+        if numel is not None and (t.numel() != numel or not t.is_contiguous()):
+            raise ValueError("%s must be contiguous with %d elements" % (name, numel))
+    with torch.cuda.device(A.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(A.device).cuda_stream
+        rc = load().nsli_map_reduce_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), int(A.stride(0)),
+                                            _ptr(b), _ptr(norms2), _ptr(x), _ptr(y), _ptr(violated),
+                                            _ptr(max_viol), ctypes.c_void_p(stream) if stream else None)
     _check(rc, "nsli_map_reduce_noalloc")
 
 
