@@ -67,6 +67,10 @@ enum {
 enum {
     NSLI_OK = 0,
     NSLI_NOT_CONVERGED = 1,    /* max_iter reached without the stop rule     */
+    NSLI_RUNNING = 2,          /* nsli_get_result only: the run goes on       */
+    NSLI_CANDIDATE = 3,        /* nsli_get_result only: the stop test passed in
+                                  the accumulation type; the binary64 check
+                                  (nsli_residual_max) decides                */
     NSLI_ERR_ARG = -1,         /* invalid argument                           */
     NSLI_ERR_ZERO_ROW = -2,    /* a row of A is zero (the method needs a_i != 0) */
     NSLI_ERR_NONFINITE = -3,   /* NaN or Inf in A, b, Av, x or norms         */
@@ -93,7 +97,8 @@ typedef struct {
     int64_t iters;            /* x-updates performed by this call               */
     int64_t tick;             /* tick k after the call                          */
     int32_t status;           /* NSLI_OK, NSLI_NOT_CONVERGED or an error code   */
-    int32_t reserved;
+    int32_t rejected;         /* nsli_solve: stop candidates of the accumulation
+                                 type that the binary64 check rejected      */
     int64_t h;                /* violated rows at the final point (binary64 check) */
     double max_viol;          /* max_i (a_i.x - b_i(k)), binary64, stored A      */
     double max_viol_norm;     /* max_i (a_i.x - b_i(k)) / ||a_i||, binary64      */
@@ -245,9 +250,55 @@ int nsli_get_norms2(nsli_handle h, double *out);
  * slot is beyond CTA 0's rows); the handle stays usable.  Synchronises. */
 int nsli_test_inject_timeout(nsli_handle h, int32_t slot);
 
-/* Progress of the last nsli_iterate / nsli_solve (device state).  The
- * binary64 fields of out are those of the last check made, or 0.  Synchronises. */
+/* Progress of the last nsli_iterate / nsli_solve / sharded run (device
+ * state): status NSLI_RUNNING while a run can go on, NSLI_CANDIDATE after a
+ * stop test passed in the accumulation type and before a binary64 check
+ * decided, else NSLI_OK / NSLI_NOT_CONVERGED.  The binary64 fields of out
+ * are those of the last check made, or 0.  Synchronises. */
 int nsli_get_result(nsli_handle h, nsli_result *out);
+
+/* ---- Row shards: ModAPL (Section 3) ----
+ * Section 3 splits the list of inequalities among workers: each worker maps
+ * and reduces its own sublist, the partial results are added, and the step
+ * is taken with the sums.  Here each worker is a handle created (as usual,
+ * with nsli_create / nsli_create_csr) over a contiguous block of rows of
+ * the whole system, with the same x0; normally one handle per GPU of a
+ * process group.  One iteration is
+ *   nsli_shard_map(h_w, rec_w)                 on every worker w,
+ *   gather rec_0 .. rec_{R-1} into `records`   (an allgather, in worker order),
+ *   nsli_shard_step(h_w, records, R, 0)        on every worker w.
+ * A record is NSLI_SHARD_HEADER + n doubles: h_w, max_i r_i, max_i r_i /
+ * ||a_i|| and max_i |b_i(k)| over the worker's rows (binary32 / bf16 / fp8
+ * storage: accumulation-type values), then y_w (its Reduce, Eq. 7-8).  The
+ * step adds the y_w in worker order in binary64 (a fixed order: identical
+ * records give identical iterates on every worker, without a broadcast of
+ * x), adds the h_w, takes the maxima, then makes the same stop decision and
+ * step as nsli_iterate / nsli_solve (Eq. 8 relaxed or Eq. 12).  Results
+ * differ from a single handle over all rows only by the order of the sums. */
+#define NSLI_SHARD_HEADER 4
+
+/* Set the run parameters of a sharded run on this worker (as a solve does:
+ * iteration count 0, tick kept; p->max_iter bounds the updates; p->stop is
+ * tested by nsli_shard_step on the combined values, a pass leaving status
+ * "candidate" for the caller's binary64 check).  Call it with the same
+ * parameters on every worker.  Allocates the step's partial sums on first
+ * use.  Asynchronous. */
+int nsli_shard_begin(nsli_handle h, const nsli_params *p);
+
+/* Map and local Reduce of this worker's rows at its current x and tick;
+ * writes the record to `record` (device memory of the handle's device,
+ * NSLI_SHARD_HEADER + n doubles).  Runs even after a finished run.
+ * Asynchronous on the handle's stream. */
+int nsli_shard_map(nsli_handle h, double *record);
+
+/* The global Reduce of `nranks` records (device memory, nranks x
+ * (NSLI_SHARD_HEADER + n) doubles, worker order), the stop decision and the
+ * step, on this worker's x.  Does nothing once the run has stopped (a
+ * candidate, the step rule, or max_iter) unless force_step != 0, which
+ * resumes the run and steps without testing (after a rejected candidate).
+ * Progress is read with nsli_get_result.  Asynchronous on the handle's
+ * stream: the records must be complete in stream order when it runs. */
+int nsli_shard_step(nsli_handle h, const double *records, int32_t nranks, int32_t force_step);
 
 /* Map + Reduce of a caller-held binary32 system that ALLOCATES NOTHING (the
  * paper has no counterpart; this is an interface for callers that cannot
@@ -355,6 +406,36 @@ int nsli_pool_set_ticks(nsli_pool pool, const int64_t *slots, const int64_t *tic
  * cap). */
 int nsli_pool_poll(nsli_pool pool, int64_t *slots, int32_t *status, int64_t *iters,
                    int64_t cap, int64_t *count);
+
+/* Persistent serving: ONE launch iterates every live problem round after
+ * round (Map items of all problems, grid barrier, Reduce-and-step items,
+ * grid barrier, control) until nsli_pool_yield is called, no problem is
+ * left running, max_rounds rounds have run, or max_seconds have passed.
+ * The kernel is a cooperative launch with one CTA per SM.  tick_s > 0:
+ * each problem's tick is its tick when the launch began (as set by
+ * nsli_pool_set_ticks, which holds ticks) plus the wall-clock time since
+ * the launch began in units of tick_s, advanced by the kernel itself; 0:
+ * ticks advance per iteration unless held.  Problems that stop (a stop
+ * candidate, the step rule, their max_iter) are published while the launch
+ * runs through pinned host memory (nsli_pool_stopped).  While a launch
+ * runs, only nsli_pool_yield, nsli_pool_stopped, nsli_pool_wait and the
+ * counters may be called; the other pool calls return NSLI_ERR_ARG
+ * (allocation calls are implicit device synchronisation points, so
+ * admission and retirement happen between launches).  Asynchronous. */
+int nsli_pool_launch(nsli_pool pool, int64_t max_rounds, double max_seconds, double tick_s);
+
+/* Ask the running launch to end at its next round boundary (non-blocking;
+ * no effect when none runs). */
+int nsli_pool_yield(nsli_pool pool);
+
+/* Problems that stopped during the running launch so far (non-blocking,
+ * read from pinned host memory; 0 when no launch runs). */
+int64_t nsli_pool_stopped(nsli_pool pool);
+
+/* Wait for the running launch to end; *rounds (may be NULL) receives the
+ * rounds it ran.  The next nsli_pool_poll reads only the problems it
+ * reported.  NSLI_ERR_TIMEOUT if a bounded grid barrier wait expired. */
+int nsli_pool_wait(nsli_pool pool, int64_t *rounds);
 
 int nsli_pool_get_x(nsli_pool pool, int64_t slot, double *x);
 int nsli_pool_residual_max(nsli_pool pool, int64_t slot, double *max_viol,

@@ -5,6 +5,7 @@
 // CUDA graphs, and runs the solve loop (graph block, read 64-byte state,
 // binary64 confirmation of candidate stops).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -81,6 +82,9 @@ struct nsli_solver {
     size_t res_smem = 0;
     int *res_rows = nullptr, *res_cols = nullptr;
 
+    // row-sharded runs (nsli_shard_*): partial sums of the exchange step
+    double *shard_dx = nullptr;
+
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     int graph_rule = -1;
@@ -132,7 +136,7 @@ void free_all(nsli_solver *h)
         return;
     if (h->graph)
         cudaGraphExecDestroy(h->graph);
-    void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf,
+    void *dev[] = {h->A, h->meta, h->x, h->part_y, h->b0_64, h->av_64, h->n2_64, h->part_dx, h->ybuf, h->shard_dx,
                    h->dtmp, h->scale, h->part_stat, h->st, h->ver, h->flags,
                    (h->x64 != h->x) ? (void *)h->x64 : nullptr,
                    (h->n2_meta != h->n2_64) ? (void *)h->n2_meta : nullptr,
@@ -444,6 +448,8 @@ const char *nsli_strerror(int code)
     switch (code) {
     case NSLI_OK: return "ok";
     case NSLI_NOT_CONVERGED: return "maximum number of iterations reached";
+    case NSLI_RUNNING: return "running";
+    case NSLI_CANDIDATE: return "stop test passed, binary64 check pending";
     case NSLI_ERR_ARG: return "invalid argument";
     case NSLI_ERR_ZERO_ROW: return "zero row in A";
     case NSLI_ERR_NONFINITE: return "NaN or Inf in the input";
@@ -1215,6 +1221,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     // candidate forces one update, so this bound is never reached
     const long long max_blocks = p->max_iter / B + p->max_iter + 4;
     bool finished = false;
+    int rejected = 0;
     for (long long blk = 0; blk < max_blocks && !finished; ++blk) {
         if (h->resident) {
             CK(sparse_resident_launch(h->storage == NSLI_F64, h->stream, h->sp, h->res_smem, B),
@@ -1245,6 +1252,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
             } else {
                 CK(state_resume_launch(h->stream, h->st), "resume");
                 h->launches += 1;
+                rejected += 1;
             }
             continue;
         }
@@ -1259,6 +1267,7 @@ int nsli_solve(nsli_handle h, const nsli_params *p, nsli_result *out)
     r.iters = h->st_host->it;
     r.tick = h->st_host->tick;
     r.status = status;
+    r.rejected = rejected;
     r.last_step_norm = std::sqrt(h->st_host->dx2);
     h->last_check = r;
     if (out)
@@ -1405,9 +1414,72 @@ int nsli_get_result(nsli_handle h, nsli_result *out)
     r.iters = h->st_host->it;
     r.tick = h->st_host->tick;
     const int sst = h->st_host->status;
-    r.status = (sst == ST_RUNNING || sst == ST_CANDIDATE) ? NSLI_NOT_CONVERGED : sst;
+    r.status = sst == ST_RUNNING ? NSLI_RUNNING : (sst == ST_CANDIDATE ? NSLI_CANDIDATE : sst);
     r.last_step_norm = std::sqrt(h->st_host->dx2);
     *out = r;
+    return NSLI_OK;
+}
+
+// ---- row shards (ModAPL, Section 3) ----------------------------------------
+
+int nsli_shard_begin(nsli_handle h, const nsli_params *p)
+{
+    Trace trace_("nsli_shard_begin");
+    if (!h)
+        return NSLI_ERR_ARG;
+    int rc = validate_params(h, p);
+    if (rc != NSLI_OK)
+        return rc;
+    if (!h->shard_dx)
+        CK(cudaMalloc((void **)&h->shard_dx, (size_t)shard_step_blocks(h->n) * 8), "allocate exchange partials");
+    return begin_run(h, p, p->stop, p->max_iter);
+}
+
+int nsli_shard_map(nsli_handle h, double *record)
+{
+    Trace trace_("nsli_shard_map");
+    if (!h || !record)
+        return NSLI_ERR_ARG;
+    if (h->sparse) {
+        SparseArgs sa = h->sp;
+        sa.ignore_done = 1;
+        sa.mode = 1;
+        CK(sparse_row_launch(h->storage == NSLI_F64, h->stream, sa), "launch Map");
+        CK(sparse_col_launch(h->storage == NSLI_F64, h->stream, sa), "launch local Reduce");
+    } else {
+        MapArgs ma = map_args(h);
+        ma.ignore_done = 1;
+        CK(map_launch(h->storage, h->vpt, h->guard, h->G, h->consumers, h->smem, h->stream, ma), "launch Map");
+        CK(reduce_only_launch(h->storage == NSLI_F64, h->red_grid, h->stream, reduce_args(h), h->ybuf),
+           "launch local Reduce");
+    }
+    CK(shard_pack_launch(h->stream, h->st, h->ybuf, h->n, record), "write the record");
+    h->launches += 3;
+    return NSLI_OK;
+}
+
+int nsli_shard_step(nsli_handle h, const double *records, int32_t nranks, int32_t force_step)
+{
+    Trace trace_("nsli_shard_step");
+    if (!h || !records || nranks < 1)
+        return NSLI_ERR_ARG;
+    if (!h->shard_dx)
+        return set_err(h, NSLI_ERR_ARG, "nsli_shard_begin has not been called on this handle");
+    if (force_step) {
+        CK(state_resume_launch(h->stream, h->st), "resume");
+        h->launches += 1;
+    }
+    ShardStepArgs a;
+    a.recs = records;
+    a.nranks = nranks;
+    a.n = h->n;
+    a.x = h->x;
+    a.x64 = h->x64;
+    a.ybuf = h->ybuf;
+    a.part_dx = h->shard_dx;
+    a.st = h->st;
+    CK(shard_step_launch(h->storage == NSLI_F64, h->stream, a), "launch exchange step");
+    h->launches += 1;
     return NSLI_OK;
 }
 
@@ -1446,6 +1518,20 @@ struct nsli_pool_s {
     std::vector<int> live_order;             // slot ids in the current tables
     long long launches = 0;
     std::string last_error;
+
+    // persistent launches (nsli_pool_launch): host-mapped control block,
+    // device scratch, and what the last launch reported
+    ServeCtrl *ctrl_host = nullptr;          // pinned, mapped
+    ServeCtrl *ctrl_dev = nullptr;           // its device address
+    ServeSync *d_sync = nullptr;
+    long long *d_tick0 = nullptr;
+    int *d_reported = nullptr;
+    size_t cap_serve = 0;
+    size_t serve_smem = 0;
+    int serve_bps = 0;
+    bool running = false;
+    bool have_done_list = false;             // poll may restrict itself to done_slots
+    std::vector<int> done_slots;
 };
 
 namespace {
@@ -1599,12 +1685,14 @@ void nsli_pool_destroy(nsli_pool p)
             free_all(h);
             delete h;
         }
-    void *bufs[] = {p->d_probs, p->d_items, p->d_red, p->d_sts, p->d_ticks};
+    void *bufs[] = {p->d_probs, p->d_items, p->d_red, p->d_sts, p->d_ticks, p->d_sync, p->d_tick0, p->d_reported};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
     if (p->h_states)
         cudaFreeHost(p->h_states);
+    if (p->ctrl_host)
+        cudaFreeHost(p->ctrl_host);
     if (p->own_stream)
         cudaStreamDestroy(p->stream);
     delete p;
@@ -1616,6 +1704,8 @@ int nsli_pool_add(nsli_pool p, int64_t m, int64_t n, const float *A, int64_t lda
     Trace trace_("nsli_pool_add");
     if (!p || !slot || !prm)
         return NSLI_ERR_ARG;
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (m < 1 || n < 1 || lda < n || !A || !b0 || !x0)
         return perr(p, NSLI_ERR_ARG, "bad problem arguments");
     // admission by memory: the pool's budget and the device's free HBM
@@ -1663,6 +1753,8 @@ int nsli_pool_add(nsli_pool p, int64_t m, int64_t n, const float *A, int64_t lda
 
 int nsli_pool_remove(nsli_pool p, int64_t slot)
 {
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
         return NSLI_ERR_ARG;
     PCK(cudaStreamSynchronize(p->stream), "synchronize");
@@ -1682,6 +1774,8 @@ int nsli_pool_step(nsli_pool p, int32_t rounds)
     Trace trace_("nsli_pool_step");
     if (!p || rounds < 0)
         return NSLI_ERR_ARG;
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (p->dirty) {
         int rc = rebuild_tables(p);
         if (rc != NSLI_OK)
@@ -1700,6 +1794,8 @@ int nsli_pool_step(nsli_pool p, int32_t rounds)
 
 int nsli_pool_set_ticks(nsli_pool p, const int64_t *slots, const int64_t *ticks, int64_t count)
 {
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (!p || count < 0 || (count > 0 && (!slots || !ticks)))
         return NSLI_ERR_ARG;
     if (count == 0)
@@ -1728,6 +1824,8 @@ int nsli_pool_set_ticks(nsli_pool p, const int64_t *slots, const int64_t *ticks,
 int nsli_pool_poll(nsli_pool p, int64_t *slots, int32_t *status, int64_t *iters, int64_t cap, int64_t *count)
 {
     Trace trace_("nsli_pool_poll");
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (!p || !count || cap < 0 || (cap > 0 && (!slots || !status || !iters)))
         return NSLI_ERR_ARG;
     *count = 0;
@@ -1739,13 +1837,24 @@ int nsli_pool_poll(nsli_pool p, int64_t *slots, int32_t *status, int64_t *iters,
         PCK(cudaMallocHost((void **)&p->h_states, std::max<size_t>(ns, 16) * sizeof(DevState)), "pinned states");
         p->cap_states = std::max<size_t>(ns, 16);
     }
-    for (size_t sid = 0; sid < ns; ++sid)
+    // after a persistent launch only the problems it reported can have
+    // stopped; otherwise every live problem is read
+    std::vector<int> check;
+    if (p->have_done_list) {
+        check = p->done_slots;
+    } else {
+        for (size_t sid = 0; sid < ns; ++sid)
+            if (p->slots[sid])
+                check.push_back((int)sid);
+    }
+    p->have_done_list = false;
+    for (int sid : check)
         if (p->slots[sid])
             PCK(cudaMemcpyAsync(&p->h_states[sid], p->slots[sid]->st, sizeof(DevState), cudaMemcpyDeviceToHost,
                                 p->stream),
                 "read state");
     PCK(cudaStreamSynchronize(p->stream), "synchronize");
-    for (size_t sid = 0; sid < ns; ++sid) {
+    for (int sid : check) {
         nsli_solver *h = p->slots[sid];
         if (!h)
             continue;
@@ -1788,8 +1897,130 @@ int nsli_pool_poll(nsli_pool p, int64_t *slots, int32_t *status, int64_t *iters,
     return NSLI_OK;
 }
 
+int nsli_pool_launch(nsli_pool p, int64_t max_rounds, double max_seconds, double tick_s)
+{
+    Trace trace_("nsli_pool_launch");
+    if (!p || max_rounds < 0 || !(max_seconds > 0.0) || !std::isfinite(max_seconds) || !(tick_s >= 0.0) ||
+        !std::isfinite(tick_s))
+        return NSLI_ERR_ARG;
+    if (p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is already running");
+    if (p->dirty) {
+        int rc = rebuild_tables(p);
+        if (rc != NSLI_OK)
+            return rc;
+    }
+    if (p->n_live == 0)
+        return NSLI_OK;
+    if (p->n_live > kServeMaxProblems)
+        return perr(p, NSLI_ERR_UNSUPPORTED, "more live problems than one persistent launch serves");
+    if (!p->ctrl_host) {
+        PCK(cudaHostAlloc((void **)&p->ctrl_host, sizeof(ServeCtrl), cudaHostAllocMapped), "pinned control block");
+        PCK(cudaHostGetDevicePointer((void **)&p->ctrl_dev, p->ctrl_host, 0), "map control block");
+        PCK(cudaMalloc((void **)&p->d_sync, sizeof(ServeSync)), "allocate grid barrier");
+    }
+    int rc;
+    size_t cap_t = p->cap_serve, cap_r = p->cap_serve;
+    if ((rc = grow(p, &p->d_tick0, &cap_t, (size_t)p->n_live)) != NSLI_OK)
+        return rc;
+    if ((rc = grow(p, &p->d_reported, &cap_r, (size_t)p->n_live)) != NSLI_OK)
+        return rc;
+    p->cap_serve = std::min(cap_t, cap_r);
+    // the reduce phase keeps its shared block in the ring's stage area
+    const size_t smem = std::max<size_t>(p->smem, 16384);
+    if (smem != p->serve_smem || p->serve_bps == 0) {
+        int bps = 0;
+        PCK(serve_prepare(p->storage, smem, &bps), "configure persistent kernel");
+        if (bps < 1)
+            return perr(p, NSLI_ERR_UNSUPPORTED, "the persistent kernel does not fit an SM");
+        p->serve_bps = bps;
+        p->serve_smem = smem;
+    }
+    // the launch's control block and barrier start from zero
+    p->ctrl_host->yield = 0;
+    p->ctrl_host->error = 0;
+    p->ctrl_host->rounds = 0;
+    p->ctrl_host->done_count = 0;
+    PCK(cudaMemsetAsync(p->d_sync, 0, sizeof(ServeSync), p->stream), "clear grid barrier");
+    ServeArgs a;
+    a.probs = p->d_probs;
+    a.items = p->d_items;
+    a.reds = p->d_red;
+    a.nprob = p->n_live;
+    a.nitems = p->n_items;
+    a.nreds = p->n_red;
+    a.tick0 = p->d_tick0;
+    a.reported = p->d_reported;
+    a.sync = p->d_sync;
+    a.ctrl = p->ctrl_dev;
+    a.max_rounds = max_rounds;
+    a.max_ns = (unsigned long long)(max_seconds * 1e9);
+    a.tick_ns = (unsigned long long)(tick_s * 1e9);
+    if (tick_s > 0.0 && a.tick_ns == 0)
+        a.tick_ns = 1;
+    const int grid = p->serve_bps * p->num_sms;
+    PCK(serve_launch(p->storage, grid, smem, p->stream, a), "persistent launch");
+    p->launches += 1;
+    p->running = true;
+    return NSLI_OK;
+}
+
+int nsli_pool_yield(nsli_pool p)
+{
+    if (!p)
+        return NSLI_ERR_ARG;
+    if (p->running) {
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        *(volatile int *)&p->ctrl_host->yield = 1;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+    }
+    return NSLI_OK;
+}
+
+int64_t nsli_pool_stopped(nsli_pool p)
+{
+    if (!p || !p->running)
+        return 0;
+    const unsigned int c = *(volatile unsigned int *)&p->ctrl_host->done_count;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    return (int64_t)c;
+}
+
+int nsli_pool_wait(nsli_pool p, int64_t *rounds)
+{
+    Trace trace_("nsli_pool_wait");
+    if (!p)
+        return NSLI_ERR_ARG;
+    if (!p->running) {
+        if (rounds)
+            *rounds = 0;
+        return NSLI_OK;
+    }
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    p->running = false;
+    if (e != cudaSuccess)
+        return perr(p, NSLI_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    ServeCtrl *c = p->ctrl_host;
+    if (rounds)
+        *rounds = (int64_t)c->rounds;
+    p->done_slots.clear();
+    const unsigned int nd = std::min<unsigned int>(c->done_count, (unsigned int)kServeMaxProblems);
+    for (unsigned int k = 0; k < nd; ++k) {
+        const int q = c->done[k].prob;
+        if (q >= 0 && q < (int)p->live_order.size())
+            p->done_slots.push_back(p->live_order[q]);
+    }
+    p->have_done_list = true;
+    if (c->error)
+        return perr(p, NSLI_ERR_TIMEOUT, "a grid barrier wait of the persistent launch expired");
+    return NSLI_OK;
+}
+
 int nsli_pool_get_x(nsli_pool p, int64_t slot, double *x)
 {
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
         return NSLI_ERR_ARG;
     return nsli_get_x(p->slots[slot], x);
@@ -1797,6 +2028,8 @@ int nsli_pool_get_x(nsli_pool p, int64_t slot, double *x)
 
 int nsli_pool_residual_max(nsli_pool p, int64_t slot, double *max_viol, double *max_viol_norm)
 {
+    if (p && p->running)
+        return perr(p, NSLI_ERR_ARG, "a persistent launch is running: call nsli_pool_wait first");
     if (!p || slot < 0 || slot >= (int64_t)p->slots.size() || !p->slots[slot])
         return NSLI_ERR_ARG;
     return nsli_residual_max(p->slots[slot], max_viol, max_viol_norm);

@@ -66,7 +66,7 @@ __host__ __device__ __forceinline__ bool step_norm_below(double dx2, double eps)
     return sqrt(dx2) < eps;
 }
 
-enum : int { ST_RUNNING = 2, ST_CANDIDATE = 3 };
+enum : int { ST_RUNNING = 2, ST_CANDIDATE = 3 };   // reported as NSLI_RUNNING / NSLI_CANDIDATE
 enum : int { ERRF_TIMEOUT = 1 };
 enum : int { PREPF_ZERO_ROW = 1, PREPF_NONFINITE = 2 };
 
@@ -128,6 +128,44 @@ struct GroupRed {
     int blk;            // block index within the problem
 };
 
+// Persistent serving (one launch iterates all live problems of a pool for
+// many rounds).  ServeCtrl lives in pinned, mapped host memory: the host
+// raises `yield`, the kernel publishes the problems that stopped (done[],
+// done_count) and the rounds it ran.
+struct ServeDone {
+    int prob;            // index into the launch's problem table
+    int status;          // ST_CANDIDATE, NSLI_OK or NSLI_NOT_CONVERGED
+    long long it;        // x-updates made in the problem's run
+};
+constexpr int kServeMaxProblems = 4096;
+struct ServeCtrl {
+    int yield;                    // host -> kernel: end at the next round boundary
+    int error;                    // kernel -> host: a grid barrier wait expired
+    unsigned long long rounds;    // kernel -> host: rounds completed
+    unsigned int done_count;      // kernel -> host: entries of done[] written
+    unsigned int pad;
+    ServeDone done[kServeMaxProblems];
+};
+// Device-side scratch of one launch (zeroed before it).
+struct ServeSync {
+    unsigned int bar_count, bar_gen;  // grid barrier
+    unsigned int ndone;               // completions reported
+    int stop;                         // decision of the control phase
+};
+struct ServeArgs {
+    const GroupProblem *probs;
+    const GroupItem *items;
+    const GroupRed *reds;
+    int nprob, nitems, nreds;
+    long long *tick0;          // nprob: each problem's tick when the launch began
+    int *reported;             // nprob: stop already reported (or stopped before the launch)
+    ServeSync *sync;
+    ServeCtrl *ctrl;           // host-mapped
+    long long max_rounds;
+    unsigned long long max_ns; // wall-clock bound of the launch
+    unsigned long long tick_ns;  // > 0: tick = tick0 + (now - launch) / tick_ns
+};
+
 struct VerifyArgs {
     const void *A;
     const double *x64;
@@ -164,6 +202,10 @@ cudaError_t map_group_launch(int storage, int items, size_t smem, cudaStream_t s
                              const GroupItem *it);
 cudaError_t reduce_group_launch(bool f64, int blocks, cudaStream_t s, const GroupProblem *probs,
                                 const GroupRed *tab);
+
+// persistent serving: cooperative launch of `grid` CTAs (at most one wave)
+cudaError_t serve_prepare(int storage, size_t smem, int *blocks_per_sm);
+cudaError_t serve_launch(int storage, int grid, size_t smem, cudaStream_t s, const ServeArgs &a);
 
 struct PrepArgs {
     const void *src;        // staged source rows (device), row pitch lda
@@ -234,6 +276,24 @@ cudaError_t state_resume_launch(cudaStream_t s, DevState *st);
 cudaError_t set_ticks_launch(cudaStream_t s, DevState *const *sts, const long long *ticks, int count);
 cudaError_t stored_rows_launch(int storage, cudaStream_t s, const void *A, const float *scale, long long ld,
                                long long n, long long row0, long long rows, double *out);
+
+// ---- row shards (nsli_shard.cu) ---------------------------------------------
+// A worker's record: h, max r_i, max r_i / ||a_i||, max |b_i| (doubles),
+// then y (n doubles); see include/nsli.h.
+constexpr int kShardHeader = 4;
+struct ShardStepArgs {
+    const double *recs;   // nranks records of n + kShardHeader doubles, worker order
+    int nranks;
+    long long n;
+    void *x;              // accumulation-type copy read by the Map
+    double *x64;          // binary64 iterate
+    double *ybuf;         // n doubles (ModAP: the global y)
+    double *part_dx;      // shard_step_blocks(n) partial sums
+    DevState *st;
+};
+int shard_step_blocks(long long n);
+cudaError_t shard_pack_launch(cudaStream_t s, const DevState *st, const double *ybuf, long long n, double *rec);
+cudaError_t shard_step_launch(bool f64, cudaStream_t s, const ShardStepArgs &a);
 
 // ---- sparse A (nsli_sparse.cu) ----------------------------------------------
 // A held as CSR (rows, for the residuals) and CSC (columns, for y), values

@@ -764,13 +764,14 @@ const void *long_fn(int storage, int rg, bool sy)
 // from the per-CTA records (exact integer sum / exact maxima), so all blocks
 // take the same decision.  The last block to finish (ticket) completes the
 // step.
-struct ReduceShared {
-    double part[8][32];
-    double red[8];
+template <int NGRP> struct ReduceSharedT {
+    double part[NGRP][32];
+    double red[NGRP];
     long long h;
     double mv, mn, mb;
     int last;
 };
+using ReduceShared = ReduceSharedT<8>;
 
 __device__ __forceinline__ unsigned long long red_ord_enc(double d)
 {
@@ -783,7 +784,7 @@ __device__ __forceinline__ double red_ord_dec(unsigned long long u)
     return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceShared &sh)
+template <typename SH> __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, SH &sh)
 {
     const int lane = threadIdx.x & 31;
     // maxima as order-preserving integers: exact, and no binary64 compare
@@ -815,14 +816,16 @@ __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, ReduceSh
     }
 }
 
-// Column block `blk` of `nblk` of one problem's reduce-and-step.
-template <typename Acc>
-__device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, const int nblk)
+// Column block `blk` of `nblk` of one problem's reduce-and-step, by a block
+// of NGRP warps (NGRP groups of partial rows per column: 8 in the
+// reduce kernels, 16 in the persistent serving kernel).
+template <typename Acc, int NGRP = 8>
+__device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, const int nblk,
+                                            ReduceSharedT<NGRP> &sh)
 {
     DevState *st = p.st;
     if (*(volatile int *)&st->done)
         return;
-    __shared__ ReduceShared sh;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     reduce_stats(p.part_stat, p.G, sh);
     __syncthreads();
@@ -843,24 +846,25 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
         double yj = 0.0;
         if (j < p.ld) {
             const Acc *py = static_cast<const Acc *>(p.part_y);
-            // the partial rows g = grp, grp + 8, ... added in that order in
-            // the accumulation type (binary64 is slow on this part), the
-            // eight group sums then in binary64
+            // the partial rows g = grp, grp + NGRP, ... added in that order
+            // in the accumulation type (binary64 is slow on this part), the
+            // NGRP group sums then in binary64
             if constexpr (sizeof(Acc) == 8) {
-                // binary64: four running sums (g = grp + 8 (4c + u)), added
-                // in a tree; a dependent binary64 add costs ~435 cycles here
+                // binary64: four running sums (g = grp + NGRP (4c + u)),
+                // added in a tree; a dependent binary64 add costs ~435
+                // cycles here
                 double a[4] = {0.0, 0.0, 0.0, 0.0};
-                for (int g = grp; g < p.G; g += 32) {
+                for (int g = grp; g < p.G; g += 4 * NGRP) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        if (g + 8 * u < p.G)
-                            a[u] += py[(long long)(g + 8 * u) * p.ld + j];
+                        if (g + NGRP * u < p.G)
+                            a[u] += py[(long long)(g + NGRP * u) * p.ld + j];
                 }
                 yj = (a[0] + a[1]) + (a[2] + a[3]);
             } else {
                 Acc t = Acc(0);
 #pragma unroll 8
-                for (int g = grp; g < p.G; g += 8)
+                for (int g = grp; g < p.G; g += NGRP)
                     t += py[(long long)g * p.ld + j];
                 yj = (double)t;
             }
@@ -870,12 +874,12 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
     __syncthreads();
     if (step && grp == 0) {
         double y = 0.0;
-        if constexpr (sizeof(Acc) == 8) {
+        if constexpr (sizeof(Acc) == 8 && NGRP == 8) {
             y = ((sh.part[0][lane] + sh.part[1][lane]) + (sh.part[2][lane] + sh.part[3][lane])) +
                 ((sh.part[4][lane] + sh.part[5][lane]) + (sh.part[6][lane] + sh.part[7][lane]));
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < NGRP; ++q)
                 y += sh.part[q][lane];
         }
         double val = 0.0;
@@ -937,11 +941,11 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             v = warp_sum(v);
             __syncthreads();
             if (lane == 0)
-                sh.part[0][grp] = v;
+                sh.red[grp] = v;
             __syncthreads();
             double t = 0.0;
-            for (int q = 0; q < 8; ++q)
-                t += sh.part[0][q];
+            for (int q = 0; q < NGRP; ++q)
+                t += sh.red[q];
             dx2 = t;
         } else {
             dx2 = tot;
@@ -977,16 +981,18 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
 template <typename Acc>
 __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
 {
-    reduce_body<Acc>(p, blockIdx.x, gridDim.x);
+    __shared__ ReduceShared sh;
+    reduce_body<Acc>(p, blockIdx.x, gridDim.x, sh);
 }
 
 // Many problems in one launch: block b serves (problem, column block) tab[b].
 template <typename Acc>
 __global__ void __launch_bounds__(256) reduce_group_kernel(const GroupProblem *probs, const GroupRed *tab)
 {
+    __shared__ ReduceShared sh;
     const GroupRed t = tab[blockIdx.x];
     const GroupProblem &gp = probs[t.prob];
-    reduce_body<Acc>(gp.red, t.blk, gp.red_blocks);
+    reduce_body<Acc>(gp.red, t.blk, gp.red_blocks, sh);
 }
 
 // Map + Reduce without a step (diagnostics and parity): y in binary64.
@@ -1023,6 +1029,173 @@ __global__ void __launch_bounds__(256) reduce_only_kernel(const ReduceArgs p, do
             p.st->maxnorm = sh.mn;
             p.st->maxb = sh.mb;
         }
+    }
+}
+
+// ------------------------------------------------- persistent serving ----
+//
+// One cooperative launch (every CTA resident, one per SM) iterates all live
+// problems of a pool round after round:
+//   control   CTA 0: wall-clock ticks, problems that stopped in the last
+//             round go to the host-mapped completion list, the stop decision
+//             (host yield, nothing left running, round or time bound);
+//   Map       CTAs take the work items (a block of rows of one problem)
+//             i = blockIdx.x, blockIdx.x + grid, ...;
+//   Reduce    the same for the (problem, column block) items;
+// with a grid barrier after each phase.  A problem's items and their
+// arithmetic are those of the grouped launches, so its iterates do not
+// depend on the other problems or on which CTA ran which item.  Every
+// barrier wait is bounded: on expiry the CTA records the error and returns
+// (the others then expire too).
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The serving kernel keeps its few shared words in the tail of the Map
+// ring's header (free for a binary32 accumulator: the barriers and warp sums
+// end at byte 1280), and the reduce's shared block in the ring's stages
+// (idle during the Reduce phase), so it needs no shared memory beyond the
+// largest ring of its problems.
+struct ServeShared {
+    unsigned long long t_start;
+    int ok, running;
+};
+constexpr int kServeSharedOffset = 2048;
+static_assert(kServeSharedOffset + sizeof(ServeShared) <= kSmemHeader, "serving words fit the ring header");
+static_assert(256 + 2 * kMapRowGroup * 32 * sizeof(float) <= kServeSharedOffset, "ring header layout");
+__device__ __forceinline__ ServeShared &serve_shared()
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    return *reinterpret_cast<ServeShared *>(smem + kServeSharedOffset);
+}
+
+// Grid barrier over nblocks resident CTAs: sense by generation count.
+__device__ __forceinline__ bool serve_grid_sync(ServeSync *sy, unsigned int nblocks)
+{
+    int &ok = serve_shared().ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &sy->bar_gen;
+        const unsigned int g = *gen;          // before arriving
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&sy->bar_count, 1u) + 1u;
+        int good = 1;
+        if (arrived == nblocks) {
+            atomicExch(&sy->bar_count, 0u);   // reset before the release
+            __threadfence();
+            atomicAdd(&sy->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            for (unsigned int it = 0; *gen == g; ++it) {
+                if ((it & 63u) == 63u && clock64() - t0 > kWaitLimitCycles) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Control phase (CTA 0).
+__device__ __forceinline__ void serve_control(const ServeArgs &a, long long round, unsigned long long t_start)
+{
+    int &running = serve_shared().running;
+    if (threadIdx.x == 0)
+        running = 0;
+    __syncthreads();
+    const unsigned long long now = global_ns();
+    int mine = 0;
+    for (int q = threadIdx.x; q < a.nprob; q += blockDim.x) {
+        DevState *st = a.probs[q].red.st;
+        if (round == 0) {
+            a.tick0[q] = st->tick;
+            a.reported[q] = *(volatile int *)&st->done;   // stopped before this launch
+        }
+        const int done = *(volatile int *)&st->done;
+        if (done && !a.reported[q]) {
+            a.reported[q] = 1;
+            const unsigned int k = atomicAdd(&a.sync->ndone, 1u);
+            if (k < (unsigned int)kServeMaxProblems) {
+                ServeDone d;
+                d.prob = q;
+                d.status = st->status;
+                d.it = st->it;
+                a.ctrl->done[k] = d;
+            }
+        }
+        if (!done) {
+            ++mine;
+            if (a.tick_ns > 0)
+                st->tick = a.tick0[q] + (long long)((now - t_start) / a.tick_ns);
+        }
+    }
+    if (mine)
+        atomicAdd(&running, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence_system();
+        *(volatile unsigned int *)&a.ctrl->done_count = a.sync->ndone;
+        *(volatile unsigned long long *)&a.ctrl->rounds = (unsigned long long)round;
+        const int yield = *(volatile int *)&a.ctrl->yield;
+        a.sync->stop = (yield || running == 0 || round >= a.max_rounds || now - t_start > a.max_ns) ? 1 : 0;
+        __threadfence_system();
+    }
+}
+
+template <int S, int VPT>
+__global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeArgs a)
+{
+    using Acc = typename Traits<S>::acc;
+    static_assert(sizeof(Acc) == 4, "the serving kernel keeps its words in a binary32 ring header");
+    constexpr int NGRP = kMapMaxConsumers / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    ReduceSharedT<NGRP> &rsh = *reinterpret_cast<ReduceSharedT<NGRP> *>(smem + kSmemHeader);
+    ServeShared &ss = serve_shared();
+    if (threadIdx.x == 0)
+        ss.t_start = global_ns();
+    __syncthreads();
+    const unsigned long long t_start = ss.t_start;
+    const unsigned int G = gridDim.x;
+    for (long long round = 0;; ++round) {
+        if (blockIdx.x == 0)
+            serve_control(a, round, t_start);
+        if (!serve_grid_sync(a.sync, G))
+            break;
+        if (*(volatile int *)&a.sync->stop)
+            break;
+        for (int i = blockIdx.x; i < a.nitems; i += G) {
+            const GroupItem it = a.items[i];
+            const GroupProblem &gp = a.probs[it.prob];
+            if (!*(volatile int *)&gp.map.st->done)
+                map_body<S, VPT, true, true>(gp.map, it.row_begin, it.row_end,
+                                             static_cast<Acc *>(gp.map.part_y) + (long long)it.part * gp.map.ld,
+                                             gp.map.part_stat + it.part, gp.nt, gp.vpt);
+            __syncthreads();   // every warp has left the ring before it is armed again
+        }
+        if (!serve_grid_sync(a.sync, G))
+            break;
+        for (int i = blockIdx.x; i < a.nreds; i += G) {
+            const GroupRed t = a.reds[i];
+            const GroupProblem &gp = a.probs[t.prob];
+            reduce_body<Acc, NGRP>(gp.red, t.blk, gp.red_blocks, rsh);
+            __syncthreads();
+        }
+        if (!serve_grid_sync(a.sync, G))
+            break;
+    }
+    if (threadIdx.x == 0 && *(volatile int *)&a.sync->stop == 0) {
+        // left on an expired barrier wait
+        atomicOr(&a.ctrl->error, 1);
+        __threadfence_system();
     }
 }
 
@@ -1417,6 +1590,35 @@ cudaError_t map_group_launch(int storage, int items, size_t smem, cudaStream_t s
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+static const void *serve_fn(int storage)
+{
+    if (storage == NSLI_BF16)
+        return (const void *)serve_kernel<NSLI_BF16, 4>;
+    if (storage == NSLI_F32)
+        return (const void *)serve_kernel<NSLI_F32, 8>;
+    return nullptr;
+}
+
+cudaError_t serve_prepare(int storage, size_t smem, int *blocks_per_sm)
+{
+    const void *fn = serve_fn(storage);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kMapMaxConsumers, smem);
+}
+
+cudaError_t serve_launch(int storage, int grid, size_t smem, cudaStream_t s, const ServeArgs &a)
+{
+    const void *fn = serve_fn(storage);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    void *args[] = {(void *)&a};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kMapMaxConsumers), args, smem, s);
 }
 
 cudaError_t reduce_group_launch(bool f64, int blocks, cudaStream_t s, const GroupProblem *probs,

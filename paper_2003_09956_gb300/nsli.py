@@ -22,7 +22,7 @@ from . import _build
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 RULE_RELAXED, RULE_MODAP = 0, 1
 STOP_NONE, STOP_STEP, STOP_EPSMEM, STOP_MAXVIOL_REL = 0, 1, 2, 3
-OK, NOT_CONVERGED = 0, 1
+OK, NOT_CONVERGED, RUNNING, CANDIDATE = 0, 1, 2, 3
 ERR_ARG, ERR_ZERO_ROW, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = (
     -1, -2, -3, -4, -5, -6, -7)
 
@@ -41,13 +41,13 @@ class nsli_params(ctypes.Structure):
 
 class nsli_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("tick", ctypes.c_int64),
-                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rejected", ctypes.c_int32),
                 ("h", ctypes.c_int64), ("max_viol", ctypes.c_double),
                 ("max_viol_norm", ctypes.c_double), ("max_abs_b", ctypes.c_double),
                 ("last_step_norm", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class NsliError(RuntimeError):
@@ -66,13 +66,15 @@ EXPORTS = ["nsli_create", "nsli_create_csr", "nsli_update_b", "nsli_update_rows"
            "nsli_get_stored_rows", "nsli_get_norms2", "nsli_test_inject_timeout",
            "nsli_get_result", "nsli_launch_count", "nsli_sync", "nsli_destroy",
            "nsli_strerror", "nsli_last_error", "nsli_map_reduce_noalloc",
+           "nsli_shard_begin", "nsli_shard_map", "nsli_shard_step",
            "nsli_batch_create", "nsli_batch_iterate", "nsli_batch_map_reduce", "nsli_batch_get_x",
            "nsli_batch_residual_max", "nsli_batch_launch_count", "nsli_batch_sync",
            "nsli_batch_destroy", "nsli_batch_last_error",
            "nsli_pool_create", "nsli_pool_add", "nsli_pool_step", "nsli_pool_set_ticks",
            "nsli_pool_poll", "nsli_pool_get_x", "nsli_pool_residual_max", "nsli_pool_remove",
            "nsli_pool_live", "nsli_pool_bytes_used", "nsli_pool_launch_count", "nsli_pool_sync",
-           "nsli_pool_destroy", "nsli_pool_last_error"]
+           "nsli_pool_destroy", "nsli_pool_last_error",
+           "nsli_pool_launch", "nsli_pool_yield", "nsli_pool_stopped", "nsli_pool_wait"]
 
 
 def library_path() -> str:
@@ -135,6 +137,12 @@ def load(path: str | None = None):
         lib.nsli_last_error.restype = ctypes.c_char_p
         lib.nsli_map_reduce_noalloc.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, P]
         lib.nsli_map_reduce_noalloc.restype = ctypes.c_int
+        lib.nsli_shard_begin.argtypes = [H, ctypes.POINTER(nsli_params)]
+        lib.nsli_shard_begin.restype = ctypes.c_int
+        lib.nsli_shard_map.argtypes = [H, P]
+        lib.nsli_shard_map.restype = ctypes.c_int
+        lib.nsli_shard_step.argtypes = [H, P, i32, i32]
+        lib.nsli_shard_step.restype = ctypes.c_int
         lib.nsli_batch_create.argtypes = [ctypes.POINTER(H), i64, i64, i32, P, i64, P, P, P, P, P]
         lib.nsli_batch_create.restype = ctypes.c_int
         lib.nsli_batch_iterate.argtypes = [H, ctypes.POINTER(nsli_params), i64]
@@ -179,6 +187,14 @@ def load(path: str | None = None):
         lib.nsli_pool_destroy.restype = None
         lib.nsli_pool_last_error.argtypes = [H]
         lib.nsli_pool_last_error.restype = ctypes.c_char_p
+        lib.nsli_pool_launch.argtypes = [H, i64, d, d]
+        lib.nsli_pool_launch.restype = ctypes.c_int
+        lib.nsli_pool_yield.argtypes = [H]
+        lib.nsli_pool_yield.restype = ctypes.c_int
+        lib.nsli_pool_stopped.argtypes = [H]
+        lib.nsli_pool_stopped.restype = i64
+        lib.nsli_pool_wait.argtypes = [H, ctypes.POINTER(i64)]
+        lib.nsli_pool_wait.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -234,6 +250,23 @@ def _sync_torch_inputs(*arrays):
             import torch
             torch.cuda.current_stream(a.device).synchronize()
             return
+
+
+SHARD_HEADER = 4
+
+
+def _check_record(t, n, rows):
+    """A record array for the shard calls: a contiguous CUDA float64 tensor
+    of rows x (SHARD_HEADER + n) elements (rows None: any whole number);
+    returns the number of records."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype.itemsize != 8 or not t.is_floating_point():
+        raise ValueError("records must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("records must be contiguous")
+    per = SHARD_HEADER + n
+    if t.numel() % per != 0 or t.numel() == 0 or (rows is not None and t.numel() != rows * per):
+        raise ValueError("records must hold whole records of %d doubles" % per)
+    return t.numel() // per
 
 
 def map_reduce_noalloc(A, b, norms2, x, y, violated, max_viol, stream=None):
@@ -391,6 +424,31 @@ class Solver:
         _check(load().nsli_residual_max(self._h, ctypes.byref(a), ctypes.byref(b)),
                "nsli_residual_max", self._h)
         return a.value, b.value
+
+    # -- row shards (ModAPL): see nsli_shard_* in include/nsli.h
+    def shard_begin(self, lam=1.0, rule="relaxed", stop="none", eps=0.0, max_iter=0, rho=0.0):
+        p = make_params(lam=lam, rule=rule, stop=stop, eps=eps, max_iter=max_iter, rho=rho)
+        _check(load().nsli_shard_begin(self._h, ctypes.byref(p)), "nsli_shard_begin", self._h)
+
+    def shard_map(self, record):
+        """Map + local Reduce into `record` (a CUDA float64 tensor of
+        SHARD_HEADER + n elements on the handle's device)."""
+        _check_record(record, self.n, 1)
+        _check(load().nsli_shard_map(self._h, _ptr(record)), "nsli_shard_map", self._h)
+
+    def shard_step(self, records, force_step=False):
+        """Global Reduce of `records` (CUDA float64, nranks x (SHARD_HEADER +
+        n), worker order), the stop decision and the step."""
+        R = _check_record(records, self.n, None)
+        _check(load().nsli_shard_step(self._h, _ptr(records), R, int(bool(force_step))),
+               "nsli_shard_step", self._h)
+
+    def check(self):
+        """Binary64 check at the current x and tick: (max r_i, max r_i /
+        ||a_i||, max |b_i|, h)."""
+        mv, mn = self.residual_max()
+        r = self.result()
+        return mv, mn, r["max_abs_b"], r["h"]
 
     def map_reduce(self):
         y = np.empty(self.n, np.float64)
@@ -608,6 +666,22 @@ class Pool:
                     "nsli_pool_poll")
         k = min(int(cnt.value), cap)
         return [(int(sl[i]), int(st[i]), int(it[i])) for i in range(k)]
+
+    def launch(self, max_rounds=1 << 40, max_seconds=1.0, tick_s=0.0):
+        """One persistent launch over every live problem (asynchronous)."""
+        self._check(load().nsli_pool_launch(self._h, int(max_rounds), float(max_seconds), float(tick_s)),
+                    "nsli_pool_launch")
+
+    def yield_(self):
+        self._check(load().nsli_pool_yield(self._h), "nsli_pool_yield")
+
+    def stopped(self):
+        return int(load().nsli_pool_stopped(self._h))
+
+    def wait(self):
+        r = ctypes.c_int64()
+        self._check(load().nsli_pool_wait(self._h, ctypes.byref(r)), "nsli_pool_wait")
+        return int(r.value)
 
     def get_x(self, slot, n):
         x = np.empty(n, np.float64)

@@ -1,11 +1,12 @@
-"""Multi-GPU runs as independent replicas (one process per GPU).
+"""Multi-GPU benchmark runs as independent replicas (one process per GPU).
 
-Every rank solves its own system (the paper's row sharding of one problem
-needs a per-iteration exchange of y, h and the maxima; that path is not
-built here, see DESIGN).  The only cross-rank steps are timing ones: a
-barrier before and after the timed region and the maximum of the ranks'
-times, so `value` = units processed by all ranks / slowest rank's time.
-Works with any torch.distributed backend (nccl on GPUs, gloo on CPUs).
+Every rank solves its own system.  The row-sharded form of one system
+(the exchange of each worker's y, h and maxima every iteration) is in
+shard.py; the benchmark's multi-GPU runs use replicas.  The only
+cross-rank steps here are timing ones: a barrier before and after the
+timed region and the maximum of the ranks' times, so `value` = units
+processed by all ranks / slowest rank's time.  Works with any
+torch.distributed backend (nccl on GPUs, gloo on CPUs).
 """
 from __future__ import annotations
 

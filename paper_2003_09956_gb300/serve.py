@@ -3,10 +3,14 @@
 Requests (feasibility problems of mixed sizes) are queued on arrival and
 admitted in arrival order as soon as they fit the pool's memory; every
 admitted problem stays on the device (A, x, b) and advances with all other
-live problems, one grouped launch per round; finished problems are retired
-(x and the binary64 check read back, memory released), which makes room for
-queued ones.  With `tick_s` set, the right-hand side of each problem moves
-with wall-clock time: tick k = floor((now - arrival) / tick_s).
+live problems.  In the persistent mode (the default) one launch iterates
+every live problem round after round until a problem stops, the caller's
+`wake` test reports new work, or `epoch_s` passes; otherwise each round is
+one grouped Map launch and one grouped Reduce launch.  Finished problems
+are retired (x and the binary64 check read back, memory released), which
+makes room for queued ones.  With `tick_s` set, the right-hand side of each
+problem moves with wall-clock time: tick k = floor((now - arrival) /
+tick_s), advanced on the device during a persistent launch.
 
 The scheduling is host logic; every arithmetic step runs in libnsli.so.
 """
@@ -49,10 +53,13 @@ class Request:
 
 class Server:
     def __init__(self, storage="bf16", max_bytes=0, tick_s=None, rounds_per_poll=4, stream=None,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, persistent=True, epoch_s=0.05):
         self.pool = nsli.Pool(storage=storage, max_bytes=max_bytes, stream=stream)
         self.tick_s = tick_s
         self.rounds = rounds_per_poll
+        self.persistent = persistent
+        self.epoch_s = epoch_s
+        self.launches = 0
         self.clock = clock
         self.queue: list[Request] = []
         self.live: dict[int, Request] = {}
@@ -87,16 +94,34 @@ class Server:
         ticks = [int((now - self.live[s].arrival) / self.tick_s) for s in slots]
         self.pool.set_ticks(slots, ticks)
 
-    def pump(self):
-        """Admit what fits, run a few rounds, retire what finished."""
+    def _run_rounds(self, wake):
+        """Advance every live problem; returns the rounds run."""
+        if not self.persistent:
+            self.pool.step(self.rounds)
+            return self.rounds
+        t0 = self.clock()
+        self.pool.launch(max_seconds=self.epoch_s, tick_s=self.tick_s or 0.0)
+        self.launches += 1
+        while True:
+            if self.pool.stopped() > 0 or (wake is not None and wake()):
+                self.pool.yield_()
+                break
+            if self.clock() - t0 > self.epoch_s:
+                break
+            time.sleep(0.0001)
+        return self.pool.wait()
+
+    def pump(self, wake=None):
+        """Admit what fits, advance the live problems (until something
+        stopped or `wake()` reports new work), retire what finished."""
         self._admit()
         if not self.live:
             return 0
         self._ticks()
         t0 = self.clock()
         running = [r for r in self.live.values() if r.status is None]
-        self.pool.step(self.rounds)
-        self.rounds_run += self.rounds
+        rounds = self._run_rounds(wake)
+        self.rounds_run += rounds
         finished = self.pool.poll()
         now = self.clock()
         self.busy_s += now - t0
@@ -104,11 +129,11 @@ class Server:
         for r in running:
             # a running problem advances one iteration per round until it stops
             done_iters = fin_slots.get(r.slot)
-            step = self.rounds if done_iters is None else max(0, done_iters - r.iters)
+            step = rounds if done_iters is None else max(0, done_iters - r.iters)
             self.problem_iterations += step
             self.bytes_streamed += step * r.stored_bytes
             if done_iters is None:
-                r.iters += self.rounds
+                r.iters += rounds
         for slot, status, iters in finished:
             r = self.live.pop(slot)
             r.status, r.iters = status, iters

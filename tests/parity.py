@@ -231,14 +231,32 @@ def check_map_reduce(y_g, h_g, stats_g, A_eff, b, x, storage, depth, levels=64, 
     return ref
 
 
+def implied_h(ref, dx_g, lam, rule):
+    """The h of a relaxed step dx = lambda y / h, read off its largest
+    element (None for ModAP, whose step does not involve h, and for a zero
+    step).  A wrong classification or y shows up in the element checks."""
+    if rule != "relaxed" or not np.any(ref.y):
+        return None
+    j = int(np.argmax(np.abs(ref.y)))
+    if dx_g[j] == 0.0:
+        return 0
+    return int(round(lam * ref.y[j] / dx_g[j]))
+
+
 def check_dx(ref, x_before, x_after, h_g, lam, rule, tol):
     """The step x_before - x_after of the CUDA path against ref's step, with
-    the kernel's h, element by element and in norm."""
+    the kernel's h (None: implied by the step), element by element and in
+    norm."""
     x_before = np.asarray(x_before, np.float64)
     x_after = np.asarray(x_after, np.float64)
-    ref.check_h(h_g)
-    dx_ref, dB = ref.step(h_g, lam, rule)
     dx_g = x_before - x_after        # x_{k+1} = x_k - dx
+    if h_g is None:
+        h_g = implied_h(ref, dx_g, lam, rule)
+    if h_g is not None:
+        ref.check_h(h_g)
+    else:
+        h_g = max(ref.h_sure, 1)     # ModAP: the step does not depend on h
+    dx_ref, dB = ref.step(h_g, lam, rule)
     # the binary64 update x - s y and the subtraction here: a few units of x
     lim = tol * np.abs(dx_ref) + dB + 4 * 2.0 ** -53 * (np.abs(x_before) + np.abs(x_after))
     err = np.abs(dx_g - dx_ref)

@@ -60,12 +60,16 @@ def step_and_check(solver, A_eff, b_k, storage, lam=1.0, rule="relaxed", rho=0.0
     """One iteration on the device from its own x_k, checked element by
     element against the oracle's step from the same point."""
     xk = solver.get_x()
+    y_g, h_g, _ = solver.map_reduce()      # the Map the step takes (same x, same tick)
     solver.iterate(1, lam=lam, rule=rule, rho=rho)
     x1 = solver.get_x()
     m, n = A_eff.shape
-    parity.check_step(xk, x1, solver.result()["h"], A_eff, b_k, storage,
+    parity.check_step(xk, x1, h_g, A_eff, b_k, storage,
                       depth=parity.dense_y_depth(m, num_sms()), lam=lam, rule=rule, n2=n2,
                       levels=parity.dot_levels(n))
+    if rule == "relaxed":                  # and the step is lambda y / h of that Map
+        np.testing.assert_allclose(xk - x1, lam / max(h_g, 1) * y_g, rtol=1e-12,
+                                   atol=1e-15 * (np.abs(xk).max() + 1))
     return xk, x1
 
 
@@ -454,5 +458,5 @@ def test_step_size_changes_between_runs(monkeypatch, kind):
             s.iterate(1, lam=lam, rule="relaxed", rho=0.0)
             x1 = s.get_x()
             depth = parity.dense_y_depth(700, num_sms()) if kind.startswith("dense") else 700
-            parity.check_step(xk, x1, s.result()["h"], A, p["b0"], storage, depth=depth, lam=lam, n2=n2,
+            parity.check_step(xk, x1, None, A, p["b0"], storage, depth=depth, lam=lam, n2=n2,
                               levels=parity.dot_levels(300))

@@ -63,7 +63,7 @@ def check_sparse_step(s, p, storage, b_k, lam, rule, rho, n2, b_parts=None):
     x1 = s.get_x()
     ref = parity.CsrMapRef(p["rp"], p["ci"], p["val"], p["n"], b_k, parity.to_accumulation(xk, storage),
                            storage, n2=n2, b_parts=b_parts)
-    parity.check_dx(ref, xk, x1, s.result()["h"], lam, rule, parity.TOL[storage])
+    parity.check_dx(ref, xk, x1, None, lam, rule, parity.TOL[storage])
     return x1
 
 

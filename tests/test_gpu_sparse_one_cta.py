@@ -82,7 +82,7 @@ def csr_step_check(s, p, storage, k, rho, rule, lam):
     x1 = s.get_x()
     ref = parity.CsrMapRef(p["rp"], p["ci"], p["val"], p["n"], p["b0"] + shift,
                            parity.to_accumulation(xk, storage), storage, b_parts=(p["b0"], shift))
-    parity.check_dx(ref, xk, x1, s.result()["h"], lam, rule, parity.TOL[storage])
+    parity.check_dx(ref, xk, x1, None, lam, rule, parity.TOL[storage])
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])

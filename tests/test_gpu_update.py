@@ -86,7 +86,7 @@ def test_trajectory_with_matrix_changing_every_tick(storage):
             s.iterate(1, rho=1e-3)
             x1 = s.get_x()
             # the step from the device's own x_k on A(k), element by element
-            parity.check_step(xg, x1, s.result()["h"], A64, oracle.tick_b(p["b0"], p["Av"], 1e-3, k),
+            parity.check_step(xg, x1, None, A64, oracle.tick_b(p["b0"], p["Av"], 1e-3, k),
                               storage, depth=parity.dense_y_depth(m, parity.num_sms()), n2=n2,
                               levels=parity.dot_levels(n))
             if together:
