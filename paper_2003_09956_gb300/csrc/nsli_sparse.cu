@@ -219,20 +219,31 @@ __device__ StatAcc block_stats(StatAcc s, StatAcc *sh)
     return StatAcc{h, stat_dec(mv), stat_dec(mn), stat_dec(mb)};
 }
 
+// Per-thread stats in the accumulation type: maxima of binary32 values are
+// exact in binary32, and widened once per thread (StatLoc::wide) rather
+// than per row (a binary64 instruction occupies GB300's FP64 pipe for a
+// whole warp, however few of its lanes are active).
+template <typename T> struct StatLoc {
+    long long h = 0;
+    T mv = -INFINITY, mn = -INFINITY, mb = T(0);
+    __device__ StatAcc wide() const { return StatAcc{h, (double)mv, (double)mn, (double)mb}; }
+};
+
 // r_i from a finished dot; writes c_i and folds the row into the stats.
 template <typename T>
 __device__ __forceinline__ void finish_row(const SparseArgs &p, long long i, T dot, T tk,
-                                           const typename SpTraits<T>::Meta &md, StatAcc &s)
+                                           const typename SpTraits<T>::Meta &md, StatLoc<T> &s)
 {
     const T bi = fma(tk, (T)md.av, (T)md.b0);
     const T ri = dot - bi;
     const bool viol = ri > T(0);
     static_cast<T *>(p.coef)[i] = viol ? ri * (T)md.inv_n2 : T(0);
     s.h += viol ? 1 : 0;
-    s.mv = fmax(s.mv, (double)ri);
-    s.mn = fmax(s.mn, (double)(ri * (T)md.inv_n));
+    const T rn = ri * (T)md.inv_n;
+    s.mv = ri > s.mv ? ri : s.mv;
+    s.mn = rn > s.mn ? rn : s.mn;
     const T ab = bi < T(0) ? -bi : bi;
-    s.mb = fmax(s.mb, (double)ab);
+    s.mb = ab > s.mb ? ab : s.mb;
 }
 
 // Stop decision of the iteration whose Map just finished (same rules and
@@ -305,7 +316,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads, 5) spar
     const T *va = static_cast<const T *>(p.va);
     const T *x = static_cast<const T *>(p.x);
     const T tk = (T)((double)st->tick * st->rho);
-    StatAcc s{0, -INFINITY, -INFINITY, 0.0};
+    StatLoc<T> s;
     const int nblk = p.n_row_pieces + p.row_light_ctas;
 
     if ((int)blockIdx.x < p.n_row_pieces) {
@@ -342,7 +353,7 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads, 5) spar
                 finish_row(p, i, dot, tk, md, s);
         }
     }
-    const StatAcc t = block_stats(s, sh_stat);
+    const StatAcc t = block_stats(s.wide(), sh_stat);
     if (threadIdx.x == 0) {
         PartStat ps;
         ps.h = t.h;
@@ -417,26 +428,49 @@ template <typename T, int W> __global__ void __launch_bounds__(kThreads) sparse_
         const long long c0 = b * p.light_cols_per_cta;
         const long long c1 = min(c0 + p.light_cols_per_cta, p.n);
         constexpr int groups = kThreads / W;
+        constexpr int GW = 32 / W;   // columns a warp finishes per pass
         const int g = threadIdx.x / W, l = threadIdx.x % W;
+        const int lane = threadIdx.x & 31;
+        const long long wfirst = (long long)(threadIdx.x >> 5) * GW;
+        // The binary64 step of a column (col_update) is taken for 32 columns
+        // at once, one per lane: after pass t of every W passes, lane
+        // t * GW + q holds the y and index of the column of the warp's group
+        // q (a binary64 instruction occupies the FP64 pipe for a whole warp,
+        // so one lane per column would cost 32 times as much).
+        T ybuf = T(0);
+        long long jbuf = -1;
+        int t = 0;
         for (long long base = c0; base < c1; base += groups) {
             const long long j = base + g;
             T acc = T(0);
             bool valid = j < c1;
             long long e0 = 0, e1 = 0;
-            double xo = 0.0;
             if (valid) {
                 e0 = p.cp[j];
                 e1 = p.cp[j + 1];
-                if (l == 0 && p.mode == 0 && rule != NSLI_RULE_MODAP)
-                    xo = p.x64[j];   // in flight with the entries
                 valid = (e1 - e0) <= p.heavy_thr_col;
             }
             if (valid)
                 acc = seg_dot<T, W>(e0, e1, p.ri, vc, coef, l);
             const T y = group_sum<W>(acc);
-            if (valid && l == 0)
-                part += col_update(p, j, y, s_relaxed, rule, xo);
+            const int src = (lane % GW) * W;
+            const T yq = __shfl_sync(0xffffffffu, y, src);
+            const int vq = __shfl_sync(0xffffffffu, valid ? 1 : 0, src);
+            if (lane / GW == t) {
+                ybuf = yq;
+                jbuf = vq ? base + wfirst + lane % GW : -1;
+            }
+            if (++t == W) {
+                if (jbuf >= 0)
+                    part += col_update(p, jbuf, ybuf, s_relaxed, rule,
+                                       (p.mode == 0 && rule != NSLI_RULE_MODAP) ? p.x64[jbuf] : 0.0);
+                t = 0;
+                jbuf = -1;
+            }
         }
+        if (t > 0 && jbuf >= 0)
+            part += col_update(p, jbuf, ybuf, s_relaxed, rule,
+                               (p.mode == 0 && rule != NSLI_RULE_MODAP) ? p.x64[jbuf] : 0.0);
     }
     const double bsum = block_sum(part, sh_d);
     if (threadIdx.x == 0)
