@@ -90,6 +90,10 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the serving stream measured in the same run (0: none)")
     ap.add_argument("--serving-only", action="store_true", help="time only the serving stream")
+    ap.add_argument("--pool", default="pool-40",
+                    help="fixed pool timed with persistent launches in the same run ('' for none)")
+    ap.add_argument("--pool-only", action="store_true", help="time only the fixed pool's persistent launches")
+    ap.add_argument("--pool-rounds", type=int, default=20)
     ap.add_argument("--model-only", action="store_true",
                     help="time only the model system's solves (dense and compressed rows)")
     ap.add_argument("--model-seeds", type=int, default=30, help="seeds of the model-system solves")
@@ -472,7 +476,7 @@ SERVE = {"rate": 200.0, "tick_s": 0.010, "rho": 1e-4, "eps": 1e-6, "seed": 2010,
          # d ~ U(0.01, 0.1): near the polytope, as when a request follows the
          # solution of a nearby system
          "cold_budget": 300, "warm_budget": 5000, "warm_d": (0.01, 0.1),
-         "ladder": (100.0, 50.0, 25.0, 12.5)}
+         "ladder": (25.0, 12.5, 6.25), "ladder_drain_s": 8.0}
 
 
 def serving_templates(torch, seconds, rates, seed):
@@ -562,8 +566,9 @@ def serving_stream(nsli, arrivals, templates, seconds, kind, rate, drain_s):
            if feas else None,
            "round_gbs": srv.bytes_streamed / max(srv.busy_s, 1e-9) / 1e9,
            "persistent_launches": srv.launches, "gpu_launches": srv.pool.launch_count()}
-    out["sustained"] = bool(out["left_queued"] == 0 and out["left_running"] == 0 and
-                            out["completed"] == out["requests"])
+    # kept up: 95 % of the requests finished (feasible, or at their budget)
+    # by the end of the drain
+    out["sustained"] = bool(out["completed"] >= 0.95 * out["requests"])
     srv.close()
     return out
 
@@ -573,8 +578,8 @@ def time_serving(nsli, torch, seconds):
     log-uniform in [512, 16384] over 11 log-spaced classes, m = c n with c
     in {2, 4, 8}, bf16, rho = 1e-4 per 10 ms wall-clock tick): the cold
     stream at 200 requests/s, the warm stream at 200/s, and the warm stream
-    at a ladder of lower rates up to the first one served without backlog
-    (the sustainable rate)."""
+    at a ladder of lower rates down to the first one whose requests (95 %)
+    are all served by the end of a drain (the sustainable rate)."""
     cfg = SERVE
     rates = {"cold": cfg["rate"], "warm": cfg["rate"]}
     for r in cfg["ladder"]:
@@ -584,13 +589,14 @@ def time_serving(nsli, torch, seconds):
     t_gen = time.perf_counter() - t_gen
     out = {"ticks": "%g s wall clock, advanced on the device" % cfg["tick_s"], "template_setup_s": t_gen}
     out["cold_200_per_s"] = serving_stream(nsli, streams["cold"], templates, seconds, "cold", cfg["rate"],
-                                           drain_s=seconds)
+                                           drain_s=1.0)
     out["warm_200_per_s"] = serving_stream(nsli, streams["warm"], templates, seconds, "warm", cfg["rate"],
-                                           drain_s=seconds)
+                                           drain_s=2.0)
     sustainable = cfg["rate"] if out["warm_200_per_s"]["sustained"] else None
     if sustainable is None:
         for r in cfg["ladder"]:
-            res = serving_stream(nsli, streams["warm_%g" % r], templates, seconds, "warm", r, drain_s=2.0)
+            res = serving_stream(nsli, streams["warm_%g" % r], templates, seconds, "warm", r,
+                                 drain_s=cfg["ladder_drain_s"])
             out["warm_%g_per_s" % r] = res
             if res["sustained"]:
                 sustainable = r
@@ -599,6 +605,48 @@ def time_serving(nsli, torch, seconds):
     del templates
     torch.cuda.empty_cache()
     return out
+
+
+POOL = {
+    # resident bf16 problems, m = 4 n, n cycling over the sizes; one
+    # persistent launch runs `rounds` rounds over all of them
+    "pool-40": {"sizes": (1024, 2048, 4096, 8192, 16384), "nprob": 40, "seed": 2015},
+    # the same mix without the largest size, for profiler captures (3.4 GB)
+    "pool-20": {"sizes": (1024, 2048, 4096, 8192), "nprob": 20, "seed": 2015},
+}
+
+
+def time_pool_rounds(nsli, torch, name, rounds, warmup, peak):
+    """Persistent launches (one launch = `rounds` rounds, each round one
+    iteration of every resident problem) over a fixed pool of bf16
+    problems of mixed sizes: bytes of A streamed per second."""
+    from paper_2003_09956_gb300 import workloads
+
+    w = POOL[name]
+    pool = nsli.Pool(storage="bf16")
+    total = 0
+    for q in range(w["nprob"]):
+        n = int(w["sizes"][q % len(w["sizes"])])
+        p = workloads.dense_system(4 * n, n, seed=w["seed"] + q)
+        A = torch.from_numpy(p["A"]).cuda()
+        pool.add(A, p["b0"], p["x0"], Av=p["Av"], stop="none", max_iter=1 << 40, rho=1e-4)
+        total += 4 * n * n * 2
+        del A
+    for _ in range(max(1, warmup)):
+        pool.launch(max_rounds=rounds, max_seconds=60.0)
+        pool.wait()
+    l0 = pool.launch_count()
+    t0 = time.perf_counter()
+    pool.launch(max_rounds=rounds, max_seconds=60.0)
+    r = pool.wait()
+    el = time.perf_counter() - t0
+    launches = pool.launch_count() - l0
+    pool.close()
+    torch.cuda.empty_cache()
+    gbs = total * r / el / 1e9
+    return {"workload": name + " (%d bf16 problems, m = 4n, n in %s)" % (w["nprob"], list(w["sizes"])),
+            "bytes_of_A_per_round": total, "rounds": r, "ms_per_round": el / r * 1e3, "gbs": gbs,
+            "frac_of_measured_hbm": gbs / peak, "gpu_launches": launches}
 
 
 def time_cfg2(nsli, torch, steps, warmup, dist, world, peak):
@@ -764,6 +812,13 @@ def main():
             print(json.dumps({"metric": "serving solves/sec", "value": w["solves_per_s"], "unit": "solves/s",
                               "config": {"workload": "poisson-200/s mixed-size bf16 stream"}, **r}), flush=True)
         return 0
+    if args.pool_only:
+        peak, _ = measured_peak()
+        r = time_pool_rounds(nsli, torch, args.pool, args.pool_rounds, max(1, args.warmup), peak)
+        if rank == 0:
+            print(json.dumps({"metric": "persistent pool rounds GB/s", "value": r["gbs"], "unit": "GB/s",
+                              "config": {"workload": r["workload"]}, **r}), flush=True)
+        return 0
     if args.model_only:
         dense = time_model_system(nsli, seeds=args.model_seeds)
         csr = time_model_system_csr(nsli, seeds=args.model_seeds)
@@ -843,6 +898,8 @@ def main():
         variants["batched_bf16"] = time_batched(nsli, torch, args.batched, min(K, 100), W)
     if args.serve_seconds > 0 and world == 1:
         variants["serving_bf16"] = time_serving(nsli, torch, args.serve_seconds)
+    if args.pool and world == 1:
+        variants["persistent_pool_bf16"] = time_pool_rounds(nsli, torch, args.pool, args.pool_rounds, 2, peak)
     if args.cfg2:
         variants["dense-32768x8192_f32"] = time_cfg2(nsli, torch, K, W, dist, world, peak)
     if args.feasibility:

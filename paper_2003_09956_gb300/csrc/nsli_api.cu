@@ -39,6 +39,7 @@ struct nsli_solver {
     long long m = 0, n = 0, ld = 0;
     int elem_bytes = 4, epv = 4, row_bytes = 0, nv = 0;
     int vpt = 1, consumers = 32, R = 1, nstage = 2, stage_stride = 0;
+    int cluster = 0, slice_nv = 0, cluster_vpt = 0, cluster_lag = 1;   // long rows on thread-block clusters
     bool guard = true;
     size_t smem = 0;
     int G = 1, red_grid = 1, num_sms = 1;
@@ -178,6 +179,58 @@ int choose_config(nsli_solver *h)
         }
     }
     if (h->vpt == 0) {
+        // long rows, binary64 / binary32 storage: thread-block clusters that
+        // split the columns (NSLI_LONG_CLUSTER=0 turns them off, =1 turns them
+        // on for bf16 / fp8 too): the fewest CTAs per cluster (2, 4, 8,
+        // NSLI_LONG_CLUSTER_SIZE forces one) whose column slice each CTA holds
+        // in registers, with a ring of at least three row slices per CTA.
+        // Measured at n = 54000: binary32 on clusters of four 6.07 ms per Map
+        // against 7.52 ms two-pass; bf16 5.98 against 4.06 ms (a row costs
+        // the cluster ~2 us whatever its bytes), so bf16 / fp8 stay two-pass.
+        const char *cenv = std::getenv("NSLI_LONG_CLUSTER");
+        const bool wide = h->storage == NSLI_F64 || h->storage == NSLI_F32;
+        const bool use_cluster = cenv ? cenv[0] == '1' : wide;
+        if (use_cluster) {
+            const long long per_cta = (long long)vlim * kMapMaxConsumers;
+            int forced = 0;
+            if (const char *cs = std::getenv("NSLI_LONG_CLUSTER_SIZE")) {
+                const int v = std::atoi(cs);
+                if (v == 2 || v == 4 || v == 8)
+                    forced = v;
+            }
+            int C = 0;
+            for (int c = 2; c <= 8 && !C; c *= 2)
+                if ((h->nv + c - 1) / c <= per_cta && (!forced || c == forced))
+                    C = c;
+            const int slice = C ? (int)((h->nv + C - 1) / C) : 0;
+            const int stride = C ? (int)round_up((long long)slice * 16 + 32, 128) : 1;
+            const int ns = C ? std::min(8, (232448 - kSmemHeader) / stride) : 0;
+            if (C && ns >= 3) {
+                int cv = 1;
+                while ((long long)cv * kMapMaxConsumers < slice)
+                    cv *= 2;
+                int clusters = 0;
+                const size_t smem = (size_t)kSmemHeader + (size_t)ns * stride;
+                if (cluster_prepare(h->storage, cv, C, smem, &clusters) == cudaSuccess && clusters > 0) {
+                    h->cluster = C;
+                    h->slice_nv = slice;
+                    h->cluster_vpt = cv;
+                    h->cluster_lag = std::max(1, std::min(3, ns - 3));
+                    h->consumers = kMapMaxConsumers;
+                    h->guard = true;
+                    h->nstage = ns;
+                    h->stage_stride = stride;
+                    h->R = 1;
+                    h->smem = smem;
+                    h->G = (int)std::min<long long>(clusters, h->m);
+                    h->rows_base = h->m / h->G;
+                    h->rows_rem = (int)(h->m % h->G);
+                    h->red_grid = (int)((h->ld + kReduceCols - 1) / kReduceCols);
+                    return NSLI_OK;
+                }
+                cudaGetLastError();   // a shape the device cannot take: use the two-pass kernel
+            }
+        }
         // long rows: the chunked two-pass kernel (no shared-memory ring).
         // R = rows per group: the largest of 4, 2, 1 whose rows, over all
         // CTAs, take at most 160 MB between the two passes (measured at
@@ -249,6 +302,10 @@ MapArgs map_args(nsli_solver *h)
     a.stage_stride = h->stage_stride;
     a.ignore_done = 0;
     a.skip_slot = -1;
+    a.cluster = h->cluster;
+    a.slice_nv = h->slice_nv;
+    a.cluster_vpt = h->cluster_vpt;
+    a.cluster_lag = h->cluster_lag;
     return a;
 }
 
@@ -649,7 +706,8 @@ int nsli_create(nsli_handle *out, int64_t m, int64_t n, int32_t storage, int32_t
         return fail(cuda_err(h, err, "prepare A"));
     if ((rc = read_flags(h)) != NSLI_OK)
         return fail(rc);
-    CKC(map_prepare(storage, h->vpt, h->guard, h->smem), "configure Map kernel");
+    if (h->cluster == 0)
+        CKC(map_prepare(storage, h->vpt, h->guard, h->smem), "configure Map kernel");
 #undef CKC
     *out = h;
     return NSLI_OK;

@@ -94,6 +94,10 @@ struct MapArgs {
     int stage_stride;      // bytes per stage in shared memory
     int ignore_done;       // run even when the done flag is set
     int skip_slot;         // failure injection: CTA 0 never issues this slot (-1: none)
+    int cluster;           // long rows on thread-block clusters: CTAs per cluster (0: not used)
+    int slice_nv;          // ... 16-byte vectors of a row per CTA of a cluster
+    int cluster_vpt;       // ... vectors per thread (instance of the cluster kernel)
+    int cluster_lag;       // ... rows between a row's Map and the wait for its exchange (1..3)
 };
 
 struct ReduceArgs {
@@ -192,6 +196,9 @@ int map_vpt_limit(int storage);      // largest vectors-per-thread instance
 cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem);
 cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers, size_t smem,
                        cudaStream_t s, const MapArgs &a);
+// long rows on clusters of C CTAs: set the kernel's shared memory and return
+// how many clusters can be resident at once (0: the shape does not fit)
+cudaError_t cluster_prepare(int storage, int vpt, int C, size_t smem, int *clusters);
 cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a);
 cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a,
                                double *y_out);

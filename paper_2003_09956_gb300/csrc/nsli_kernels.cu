@@ -733,6 +733,320 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
     }
 }
 
+// ------------------------------------------ Map, long rows on a cluster ----
+//
+// A thread-block cluster of C CTAs (C = 2, 4 or 8, one per SM) maps a block
+// of rows whose columns it splits: CTA q of the cluster owns the vectors
+// [q S, (q + 1) S) of every row (S = slice_nv), keeps the matching slices of
+// x and of the cluster's partial y in registers, and streams its slice of
+// each row through its own ring of bulk copies (one row slice and the row's
+// record per stage).  Per row every CTA forms its partial dot (thread
+// chains, warp butterfly, the warps' sums in order), writes it into slot q
+// of the row's exchange buffer in EVERY CTA of the cluster (distributed
+// shared memory) and arrives on that CTA's exchange barrier; each CTA then
+// adds the C partials in rank order, so all of them hold the same r_i, and
+// adds the violated row's slice from its own shared-memory copy.  A is read
+// from HBM once, with no second pass.  The exchange of row k is waited for
+// D rows later (D = cluster_lag, 1..3), while the dots of rows k+1 .. k+D
+// run, so the exchange latency is not on the critical path.  Eight exchange
+// buffers suffice: a CTA sends row k only after every CTA sent row k - D,
+// i.e. after every CTA finished reading rows up to k - 2D - 1, and
+// 8 >= 2D + 1.  The ring holds the rows awaiting their exchange, the row
+// being mapped and at least one prefetched row.  Every wait is bounded; all CTAs
+// of a cluster meet at a cluster barrier before they exit, so no CTA's
+// shared memory is written after it has gone.
+__device__ __forceinline__ unsigned int cluster_rank()
+{
+    unsigned int r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned int map_to_rank(unsigned int addr, unsigned int rank)
+{
+    unsigned int r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_remote(unsigned int raddr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(raddr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_remote(unsigned int raddr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(raddr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void arrive_remote(unsigned int rbar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_cluster(unsigned int bar, unsigned int parity)
+{
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(unsigned int bar, unsigned int parity)
+{
+    const long long t0 = clock64();
+    for (unsigned int it = 0;; ++it) {
+        if (mbar_test_cluster(bar, parity))
+            return true;
+        if ((it & 255u) == 255u && clock64() - t0 > kWaitLimitCycles)
+            return false;
+    }
+}
+
+// shared-memory header of the cluster Map (within kSmemHeader)
+constexpr int kClXB = 8;        // exchange buffers (row k uses k % 8)
+constexpr int kClFull = 0;      // 8 full barriers (stages)
+constexpr int kClXbar = 64;     // 8 exchange barriers
+constexpr int kClRed = 512;     // [2][16] warp sums
+constexpr int kClXch = 1024;    // [8][8] exchanged partial dots
+static_assert(kClXch + kClXB * 8 * 8 <= kSmemHeader, "cluster Map header fits");
+
+template <int S, int VPT>
+__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const MapArgs p)
+{
+    using Tr = Traits<S>;
+    using Acc = typename Tr::acc;
+    using Meta = typename Tr::meta;
+    constexpr int EPV = Tr::EPV;
+
+    DevState *st = p.st;
+    if (!p.ignore_done && *(volatile int *)&st->done)
+        return;   // the same for every CTA of the grid
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kClFull);
+    unsigned long long *xbar = reinterpret_cast<unsigned long long *>(smem + kClXbar);
+    Acc *xch = reinterpret_cast<Acc *>(smem + kClXch);
+    Acc *red = reinterpret_cast<Acc *>(smem + kClRed);
+    unsigned char *stages = smem + kSmemHeader;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwarps = (int)blockDim.x >> 5;
+    const int C = p.cluster;
+    const unsigned int rank = cluster_rank();
+    const long long cl = blockIdx.x / C;
+    const long long row_begin = cl * p.rows_base + (cl < p.rows_rem ? cl : (long long)p.rows_rem);
+    const long long row_end = row_begin + p.rows_base + (cl < p.rows_rem ? 1 : 0);
+    const int nrows = (int)(row_end - row_begin);
+    const long long v0 = (long long)rank * p.slice_nv;
+    const int my_nv = (int)max(0ll, min((long long)p.slice_nv, (long long)p.nv - v0));
+    const unsigned int slice_bytes = (unsigned int)my_nv * 16u;
+    const unsigned int meta_off = (unsigned int)p.slice_nv * 16u;   // record after the largest slice
+    const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
+    const unsigned char *Mb = static_cast<const unsigned char *>(p.meta);
+
+    auto issue = [&](int s) {
+        const int stage = s % p.nstage;
+        const long long row = row_begin + s;
+        unsigned char *dst = stages + (size_t)stage * p.stage_stride;
+        const unsigned int fb = smem_u32(&full[stage]);
+        mbar_expect_tx(fb, slice_bytes + 32u);
+        if (slice_bytes)
+            bulk_g2s(smem_u32(dst), Ab + row * (long long)p.row_bytes + v0 * 16, slice_bytes, fb);
+        bulk_g2s(smem_u32(dst + meta_off), Mb + row * 32, 32u, fb);
+    };
+
+    if (tid == 0) {
+        for (int q = 0; q < p.nstage; ++q)
+            mbar_init(smem_u32(&full[q]), 1u);
+        for (int q = 0; q < kClXB; ++q)
+            mbar_init(smem_u32(&xbar[q]), (unsigned int)C);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_sync_all();   // every exchange barrier of the cluster is initialised
+    int issued = 0;
+    if (tid == 0) {
+        const int first = nrows < p.nstage ? nrows : p.nstage;
+        for (int q = 0; q < first; ++q)
+            issue(q);
+        issued = first;
+    }
+
+    int voff[VPT];
+    bool vok[VPT];
+    Acc xr[VPT][EPV], yr[VPT][EPV];
+    {
+        const Acc *xg = static_cast<const Acc *>(p.x);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int j = tid + v * (int)blockDim.x;
+            voff[v] = j * 16;
+            vok[v] = j < my_nv;
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                xr[v][e] = vok[v] ? xg[(v0 + j) * EPV + e] : Acc(0);
+                yr[v][e] = Acc(0);
+            }
+        }
+    }
+    const Acc tk = (Acc)((double)st->tick * st->rho);
+    long long h_loc = 0;
+    Acc mv = neg_inf<Acc>(), mn = neg_inf<Acc>(), mb = Acc(0);
+    int aborted = 0, consumed = 0;
+
+    const int D = p.cluster_lag;
+    for (int s = 0; s < nrows + D; ++s) {
+        int flag = 0;
+        if (s < nrows) {
+            const int stage = s % p.nstage;
+            flag = mbar_wait_bounded(smem_u32(&full[stage]), (unsigned int)((s / p.nstage) & 1)) ? 0 : 1;
+            consumed = s + 1;
+            const unsigned char *row = stages + (size_t)stage * p.stage_stride;
+            Acc pe = Acc(0), po = Acc(0);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                if (vok[v] && !flag) {
+                    Acc a[EPV];
+                    decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+#pragma unroll
+                    for (int e = 0; e < EPV; e += 2)
+                        fma2(pe, po, a[e], a[e + 1], xr[v][e], xr[v][e + 1]);
+                }
+            }
+            const Acc ws = warp_sum(pe + po);
+            if (lane == 0)
+                red[(s & 1) * 16 + warp] = ws;
+        }
+        if (tid == 0 && s >= D) {
+            const int t = s - D;
+            if (!mbar_wait_cluster_bounded(smem_u32(&xbar[t % kClXB]), (unsigned int)((t / kClXB) & 1)))
+                flag = 1;
+        }
+        aborted = bar_all_or((int)blockDim.x, flag);
+        if (aborted)
+            break;
+        if (tid == 0 && s >= D + 1 && issued < nrows) {
+            // the stage of row s - D - 1, finished in the previous iteration
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(issued);
+            ++issued;
+        }
+        if (warp == 0 && s < nrows) {
+            // the warps' sums in a fixed butterfly; lane q sends this CTA's
+            // partial dot of row s to CTA q
+            Acc tot = lane < nwarps ? red[(s & 1) * 16 + lane] : Acc(0);
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1)
+                tot += __shfl_xor_sync(0xffffffffu, tot, off);
+            if (lane < C) {
+                const unsigned int la = smem_u32(&xch[(s % kClXB) * 8 + rank]);
+                const unsigned int lb = smem_u32(&xbar[s % kClXB]);
+                st_remote(map_to_rank(la, (unsigned int)lane), tot);
+                arrive_remote(map_to_rank(lb, (unsigned int)lane));
+            }
+        }
+        if (s >= D) {
+            const int t = s - D;
+            Acc dot = Acc(0);
+            for (int q = 0; q < C; ++q)
+                dot += xch[(t % kClXB) * 8 + q];
+            const unsigned char *row = stages + (size_t)(t % p.nstage) * p.stage_stride;
+            const Meta md = *reinterpret_cast<const Meta *>(row + meta_off);
+            const Acc sc = (Acc)meta_scale(md);
+            const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
+            const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
+            const bool viol = ri > Acc(0);
+            const Acc c = viol ? ((S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2) : Acc(0);
+            if (warp == 0) {
+                h_loc += viol ? 1 : 0;
+                mv = ri > mv ? ri : mv;
+                const Acc rn = ri * (Acc)md.inv_n;
+                mn = rn > mn ? rn : mn;
+                const Acc ab = bi < Acc(0) ? -bi : bi;
+                mb = ab > mb ? ab : mb;
+            }
+            if (c != Acc(0)) {
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    if (vok[v]) {
+                        Acc a[EPV];
+                        decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+#pragma unroll
+                        for (int e = 0; e < EPV; e += 2)
+                            fma2(yr[v][e], yr[v][e + 1], c, c, a[e], a[e + 1]);
+                    }
+                }
+            }
+        }
+    }
+
+    if (aborted) {
+        // record the error; wait (bounded) for this CTA's copies in flight
+        if (tid == 0) {
+            atomicOr(&st->error, ERRF_TIMEOUT);
+            for (int q = consumed; q < issued; ++q)
+                mbar_wait_bounded(smem_u32(&full[q % p.nstage]), (unsigned int)((q / p.nstage) & 1));
+        }
+    } else {
+        Acc *py = static_cast<Acc *>(p.part_y) + cl * p.ld + v0 * EPV;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            if (vok[v]) {
+                const long long j = tid + v * (long long)blockDim.x;
+#pragma unroll
+                for (int e = 0; e < EPV; ++e)
+                    py[j * EPV + e] = yr[v][e];
+            }
+        }
+        if (tid == 0 && rank == 0) {
+            PartStat ps;
+            ps.h = h_loc;
+            ps.maxviol = (double)mv;
+            ps.maxnorm = (double)mn;
+            ps.maxb = (double)mb;
+            p.part_stat[cl] = ps;
+        }
+    }
+    __syncthreads();
+    cluster_sync_all();   // no CTA leaves while a peer may still write to it
+}
+
+// instances up to the register-resident limit of the storage type (8, 8,
+// 4, 2 vectors per thread for binary64, binary32, bf16, fp8)
+template <int S> constexpr int cluster_vpt_max() { return S == NSLI_BF16 ? 4 : (S == NSLI_FP8E4M3 ? 2 : 8); }
+template <int S> const void *cluster_fn_s(int vpt)
+{
+    if (vpt == 1)
+        return (const void *)map_cluster_kernel<S, 1>;
+    if (vpt == 2)
+        return (const void *)map_cluster_kernel<S, 2>;
+    if constexpr (cluster_vpt_max<S>() >= 4) {
+        if (vpt == 4)
+            return (const void *)map_cluster_kernel<S, 4>;
+    }
+    if constexpr (cluster_vpt_max<S>() >= 8) {
+        if (vpt == 8)
+            return (const void *)map_cluster_kernel<S, 8>;
+    }
+    return nullptr;
+}
+const void *cluster_fn(int storage, int vpt)
+{
+    if (vpt > map_vpt_limit(storage))
+        return nullptr;
+    switch (storage) {
+    case NSLI_F64: return cluster_fn_s<NSLI_F64>(vpt);
+    case NSLI_F32: return cluster_fn_s<NSLI_F32>(vpt);
+    case NSLI_BF16: return cluster_fn_s<NSLI_BF16>(vpt);
+    case NSLI_FP8E4M3: return cluster_fn_s<NSLI_FP8E4M3>(vpt);
+    default: return nullptr;
+    }
+}
+
 template <int S, int RG, bool SY> const void *long_fn_rg() { return (const void *)map_long_kernel<S, RG, SY>; }
 template <int S> const void *long_fn_s(int rg, bool sy)
 {
@@ -1151,6 +1465,16 @@ __device__ __forceinline__ void serve_control(const ServeArgs &a, long long roun
     }
 }
 
+template <int S, int V>
+__device__ __forceinline__ void serve_map_item(const GroupProblem &gp, const GroupItem &it,
+                                               typename Traits<S>::acc *prow, PartStat *pst)
+{
+    if (gp.nt == (int)blockDim.x && gp.nt * gp.vpt == gp.map.nv && gp.vpt == V)
+        map_body<S, V, false, false>(gp.map, it.row_begin, it.row_end, prow, pst, gp.nt, V);
+    else
+        map_body<S, V, true, true>(gp.map, it.row_begin, it.row_end, prow, pst, gp.nt, gp.vpt);
+}
+
 template <int S, int VPT>
 __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeArgs a)
 {
@@ -1175,10 +1499,21 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeA
         for (int i = blockIdx.x; i < a.nitems; i += G) {
             const GroupItem it = a.items[i];
             const GroupProblem &gp = a.probs[it.prob];
-            if (!*(volatile int *)&gp.map.st->done)
-                map_body<S, VPT, true, true>(gp.map, it.row_begin, it.row_end,
-                                             static_cast<Acc *>(gp.map.part_y) + (long long)it.part * gp.map.ld,
-                                             gp.map.part_stat + it.part, gp.nt, gp.vpt);
+            if (!*(volatile int *)&gp.map.st->done) {
+                Acc *prow = static_cast<Acc *>(gp.map.part_y) + (long long)it.part * gp.map.ld;
+                PartStat *pst = gp.map.part_stat + it.part;
+                // the instance of the problem's own vectors per thread (its
+                // rows per block barrier), guard-free when the block covers
+                // the row exactly
+                if (gp.vpt == 1)
+                    serve_map_item<S, 1>(gp, it, prow, pst);
+                else if (gp.vpt == 2)
+                    serve_map_item<S, 2>(gp, it, prow, pst);
+                else if (gp.vpt == 4 || VPT < 8)
+                    serve_map_item<S, (VPT < 4 ? VPT : 4)>(gp, it, prow, pst);
+                else
+                    serve_map_item<S, VPT>(gp, it, prow, pst);
+            }
             __syncthreads();   // every warp has left the ring before it is armed again
         }
         if (!serve_grid_sync(a.sync, G))
@@ -1549,9 +1884,52 @@ cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+cudaError_t cluster_prepare(int storage, int vpt, int C, size_t smem, int *clusters)
+{
+    *clusters = 0;
+    const void *fn = cluster_fn(storage, vpt);
+    if (!fn || C < 2 || C > 8)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kMapMaxConsumers);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
+}
+
 cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers, size_t smem, cudaStream_t s,
                        const MapArgs &a)
 {
+    if (vpt == 0 && a.cluster > 1) {
+        // long rows on clusters: `grid` clusters of a.cluster CTAs
+        const void *fn = cluster_fn(storage, a.cluster_vpt);
+        if (!fn)
+            return cudaErrorInvalidValue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(grid * a.cluster));
+        cfg.blockDim = dim3(kMapMaxConsumers);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)a.cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        void *args[] = {const_cast<MapArgs *>(&a)};
+        return cudaLaunchKernelExC(&cfg, fn, args);
+    }
     if (vpt == 0) {
         // long rows: rows_per_slot carries the group size, smem the
         // partial-sum row in shared memory (0: in global memory)

@@ -408,11 +408,45 @@ LONG = [("f32", 600, 20000), ("bf16", 300, 40000), ("fp8", 200, 70000), ("f64", 
 @pytest.mark.parametrize("budget_mb", ["8", "30", "512"])
 @pytest.mark.parametrize("storage,m,n", [("f32", 600, 20000), ("bf16", 300, 40000)])
 def test_long_rows_every_group_size(monkeypatch, budget_mb, storage, m, n):
-    """The L2 budget for the rows of a group (NSLI_LONG_L2_MB) picks one,
-    two or four rows per group; all give the oracle's step, with the
-    partial sums in shared memory."""
+    """The two-pass long-row kernel (clusters turned off): the L2 budget for
+    the rows of a group (NSLI_LONG_L2_MB) picks one, two or four rows per
+    group; all give the oracle's step, with the partial sums in shared
+    memory."""
+    monkeypatch.setenv("NSLI_LONG_CLUSTER", "0")
     monkeypatch.setenv("NSLI_LONG_L2_MB", budget_mb)
     test_long_rows_one_step_and_trajectory(storage, m, n)
+
+
+@pytest.mark.parametrize("storage,m,n", [("f32", 200, 54000), ("bf16", 300, 40000), ("f64", 200, 9000)])
+def test_long_rows_two_pass_kernel(monkeypatch, storage, m, n):
+    """The two-pass kernel (NSLI_LONG_CLUSTER=0) keeps the same parity bar."""
+    monkeypatch.setenv("NSLI_LONG_CLUSTER", "0")
+    test_long_rows_one_step_and_trajectory(storage, m, n)
+
+
+@pytest.mark.parametrize("storage,m,n,size", [("bf16", 300, 40000, "4"), ("fp8", 200, 70000, "8"),
+                                             ("f32", 400, 60000, "8"), ("f64", 200, 9000, "4")])
+def test_long_rows_cluster_kernel_every_storage_and_size(monkeypatch, storage, m, n, size):
+    """The cluster kernel forced on (bf16 / fp8 use the two-pass kernel by
+    default) and at other cluster sizes: same parity bar."""
+    monkeypatch.setenv("NSLI_LONG_CLUSTER", "1")
+    monkeypatch.setenv("NSLI_LONG_CLUSTER_SIZE", size)
+    test_long_rows_one_step_and_trajectory(storage, m, n)
+
+
+def test_long_rows_cluster_kernel_equals_two_pass_kernel_and_is_deterministic(monkeypatch):
+    """n = 54000 (the paper's size) on clusters of four CTAs: repeated runs
+    give the same bits, and the iterate agrees with the two-pass kernel's to
+    the parity tolerance after a few steps."""
+    p = workloads.dense_system(400, 54000, seed=3999)
+    xs = []
+    for cluster in ("1", "1", "0"):
+        monkeypatch.setenv("NSLI_LONG_CLUSTER", cluster)
+        with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage="f32") as s:
+            s.iterate(5, rho=1e-3)
+            xs.append(s.get_x())
+    np.testing.assert_array_equal(xs[0], xs[1])
+    assert np.linalg.norm(xs[0] - xs[2]) <= 1e-5 * np.linalg.norm(xs[2] - p["x0"])
 
 
 @pytest.mark.parametrize("storage,m,n", LONG)
