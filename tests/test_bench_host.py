@@ -43,3 +43,28 @@ def test_map_source_hash_covers_the_map_kernel():
     assert "map_body(" in src[:end] and "map_kernel(const MapArgs p)" in src[:end]
     assert "map_long_kernel(const MapArgs p)" in src[end:]
     assert len(bench.kernels_sha()) == 12
+
+
+def test_oracle_max_violation_at_a_final_iterate_matches_the_oracle():
+    """The CPU leg's max-violation error of a result: the oracle's own
+    maximum over all rows, taken per row block in threads, equals the
+    oracle over the whole matrix on each storage type's exact values."""
+    import oracle
+    from paper_2003_09956_gb300 import workloads
+
+    p = workloads.dense_system(1001, 130, seed=17)
+    x = p["x0"] * 0.3
+    for st in ("f32", "bf16", "fp8"):
+        A = p["A"] if st == "f32" else (oracle.quantize_bf16(p["A"]) if st == "bf16"
+                                        else oracle.quantize_e4m3_rows(p["A"])[0])
+        n2, _ = oracle.norms2(A)
+        ref = oracle.map_reduce(A, oracle.tick_b(p["b0"], p["Av"], 1e-3, 5), n2, x)["maxviol"]
+        r = bench.oracle_max_violation(p, (st, x, 5, 1e-3, ref + 1.0), threads=3)
+        assert r["oracle_f64"] == ref and r["threads"] == 3
+        assert abs(r["abs_diff"] - 1.0) < 1e-9
+
+
+def test_pool_and_feasibility_workloads_are_defined():
+    assert set(bench.POOL) == {"pool-40", "pool-20"}
+    for w in bench.FEASIBILITY.values():
+        assert w["m"] == 4 * w["n"]
