@@ -103,6 +103,11 @@ def parse_args():
     ap.add_argument("--cfg2", type=int, default=1, help="time the 32768 x 8192 system at rho 0, 1e-4, 1e-3")
     ap.add_argument("--feasibility", default="dense-8192x2048",
                     help="system solved to binary64-confirmed max r_i <= 1e-6 max|b| per storage ('' for none)")
+    ap.add_argument("--feasibility-only", action="store_true", help="run only the solves to feasibility")
+    ap.add_argument("--feasibility-storages", default="f32,bf16,fp8")
+    ap.add_argument("--feasibility-grid", type=int, default=1,
+                    help="1: A drawn on each storage type's grid; 0: the binary32 system rounded")
+    ap.add_argument("--feasibility-max-iter", type=int, default=1000000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -664,13 +669,18 @@ def time_pool_rounds(nsli, torch, name, rounds, warmup, peak):
     w = POOL[name]
     pool = nsli.Pool(storage="bf16")
     total = 0
+    # one template system per size (each problem gets its own device copy
+    # of it and its own x0)
+    templates = {n: workloads.dense_system(4 * n, n, seed=w["seed"] + n) for n in w["sizes"]}
     for q in range(w["nprob"]):
         n = int(w["sizes"][q % len(w["sizes"])])
-        p = workloads.dense_system(4 * n, n, seed=w["seed"] + q)
+        p = templates[n]
         A = torch.from_numpy(p["A"]).cuda()
-        pool.add(A, p["b0"], p["x0"], Av=p["Av"], stop="none", max_iter=1 << 40, rho=1e-4)
+        x0 = np.random.default_rng(w["seed"] + q).normal(0.0, 5.0, n).astype(np.float32).astype(np.float64)
+        pool.add(A, p["b0"], x0, Av=p["Av"], stop="none", max_iter=1 << 40, rho=1e-4)
         total += 4 * n * n * 2
         del A
+    del templates
     for _ in range(max(1, warmup)):
         pool.launch(max_rounds=rounds, max_seconds=60.0)
         pool.wait()
@@ -713,21 +723,27 @@ FEASIBILITY = {
     "dense-8192x2048": {"m": 8192, "n": 2048, "seed": 3001},
     "dense-16384x4096": {"m": 16384, "n": 4096, "seed": 3002},
     "dense-32768x8192": {"m": 32768, "n": 8192, "seed": 2004},
+    # the benchmark system at rho = 0 (hundreds of thousands of iterations:
+    # minutes per storage type)
+    "dense-131072x16384": {"m": 131072, "n": 16384, "seed": 2005},
 }
 
 
-def time_feasibility(nsli, name, storages=("f32", "bf16", "fp8"), max_iter=3000000):
+def time_feasibility(nsli, name, storages=("f32", "bf16", "fp8"), max_iter=1000000, on_grid=True):
     """Solves from x0 ~ N(0, 25 I) of a stationary dense random system to
     max_i r_i <= 1e-6 max|b| confirmed by the binary64 check, per storage
     (RELAXED, lambda = 1): iterations, wall time, the binary64 violation,
-    and the binary32 stop candidates the check rejected."""
+    and the binary32 stop candidates the check rejected.  on_grid: A drawn
+    on each storage type's grid (the same system for every storage);
+    otherwise the binary32 system, rounded to the storage type."""
     from paper_2003_09956_gb300 import workloads
 
     f = FEASIBILITY[name]
-    out = {"workload": name + " rho=0, RELAXED lambda=1, MAXVIOL_REL 1e-6, x0 ~ N(0, 25 I); A drawn on each "
-                              "storage type's grid, so that z is interior to the stored system"}
+    out = {"workload": name + " rho=0, RELAXED lambda=1, MAXVIOL_REL 1e-6, x0 ~ N(0, 25 I); " +
+           ("A drawn on each storage type's grid, so that z is interior to the stored system" if on_grid
+            else "A drawn in binary32 and rounded to the storage type")}
     for st in storages:
-        grid = {"f32": None, "bf16": "bf16", "fp8": "e4m3"}[st]
+        grid = {"f32": None, "bf16": "bf16", "fp8": "e4m3"}[st] if on_grid else None
         p = workloads.dense_system(f["m"], f["n"], seed=f["seed"], grid=grid)
         with nsli.Solver(p["A"], p["b0"], p["x0"], storage=st) as s:
             s.iterate(64, block_iters=64)          # warm-up (graph capture)
@@ -851,6 +867,13 @@ def main():
             w = r["warm_200_per_s"]
             print(json.dumps({"metric": "serving solves/sec", "value": w["solves_per_s"], "unit": "solves/s",
                               "config": {"workload": "poisson-200/s mixed-size bf16 stream"}, **r}), flush=True)
+        return 0
+    if args.feasibility_only:
+        r = time_feasibility(nsli, args.feasibility, storages=tuple(args.feasibility_storages.split(",")),
+                             max_iter=args.feasibility_max_iter, on_grid=bool(args.feasibility_grid))
+        if rank == 0:
+            print(json.dumps({"metric": "solve to binary64-confirmed feasibility", "config": {"workload": r["workload"]},
+                              **r}), flush=True)
         return 0
     if args.pool_only:
         peak, _ = measured_peak()

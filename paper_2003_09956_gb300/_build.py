@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libnsli.so")
 SOURCES = ["nsli_kernels.cu", "nsli_api.cu", "nsli_noalloc.cu", "nsli_batch.cu", "nsli_sparse.cu", "nsli_update.cu", "nsli_shard.cu"]
-HEADERS = [os.path.join(CSRC, "nsli_internal.h"), os.path.join(CSRC, "nsli_sumsq.cuh"), os.path.join(INCLUDE, "nsli.h")]
+HEADERS = [os.path.join(CSRC, "nsli_internal.h"), os.path.join(CSRC, "nsli_sumsq.cuh"),
+           os.path.join(CSRC, "nsli_async.cuh"), os.path.join(INCLUDE, "nsli.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -179,17 +179,15 @@ int choose_config(nsli_solver *h)
         }
     }
     if (h->vpt == 0) {
-        // long rows, binary64 / binary32 storage: thread-block clusters that
-        // split the columns (NSLI_LONG_CLUSTER=0 turns them off, =1 turns them
-        // on for bf16 / fp8 too): the fewest CTAs per cluster (2, 4, 8,
-        // NSLI_LONG_CLUSTER_SIZE forces one) whose column slice each CTA holds
-        // in registers, with a ring of at least three row slices per CTA.
-        // Measured at n = 54000: binary32 on clusters of four 6.07 ms per Map
-        // against 7.52 ms two-pass; bf16 5.98 against 4.06 ms (a row costs
-        // the cluster ~2 us whatever its bytes), so bf16 / fp8 stay two-pass.
+        // long rows: thread-block clusters that split the columns
+        // (NSLI_LONG_CLUSTER=0 selects the two-pass kernel): the fewest CTAs
+        // per cluster (2, 4, 8; NSLI_LONG_CLUSTER_SIZE forces one) whose
+        // column slice each CTA holds in registers, with a ring of at least
+        // three row slices per CTA.  Measured at n = 54000 (108001 rows):
+        // binary32 4.72 ms per Map on clusters of four against 7.52 ms
+        // two-pass, bf16 3.57 against 4.06 ms.
         const char *cenv = std::getenv("NSLI_LONG_CLUSTER");
-        const bool wide = h->storage == NSLI_F64 || h->storage == NSLI_F32;
-        const bool use_cluster = cenv ? cenv[0] == '1' : wide;
+        const bool use_cluster = !(cenv && cenv[0] == '0');
         if (use_cluster) {
             const long long per_cta = (long long)vlim * kMapMaxConsumers;
             int forced = 0;
@@ -216,6 +214,11 @@ int choose_config(nsli_solver *h)
                     h->slice_nv = slice;
                     h->cluster_vpt = cv;
                     h->cluster_lag = std::max(1, std::min(3, ns - 3));
+                    if (const char *ls = std::getenv("NSLI_LONG_CLUSTER_LAG")) {
+                        const int v = std::atoi(ls);   // 1..3, leaving a stage to prefetch
+                        if (v >= 1 && v <= 3 && v <= ns - 2)
+                            h->cluster_lag = v;
+                    }
                     h->consumers = kMapMaxConsumers;
                     h->guard = true;
                     h->nstage = ns;
@@ -1673,6 +1676,14 @@ int rebuild_tables(nsli_pool p)
         smem = std::max(smem, h->smem);
         p->live_order.push_back((int)sid);
     }
+    // The persistent launch takes the items in table order from a shared
+    // counter: put first the items that stream fewest bytes per unit of
+    // time (problems whose rows occupy fewest of the CTA's threads), so the
+    // long ones start early and the short ones fill the end of the phase.
+    // Which CTA maps an item changes no result.
+    std::stable_sort(items.begin(), items.end(), [&probs](const GroupItem &a, const GroupItem &b) {
+        return probs[a.prob].nt < probs[b.prob].nt;
+    });
     int rc;
     if ((rc = grow(p, &p->d_probs, &p->cap_probs, std::max<size_t>(1, probs.size()))) != NSLI_OK)
         return rc;

@@ -155,6 +155,7 @@ struct ServeSync {
     unsigned int bar_count, bar_gen;  // grid barrier
     unsigned int ndone;               // completions reported
     int stop;                         // decision of the control phase
+    unsigned int map_next, red_next;  // next Map / Reduce item to take (reset every round)
 };
 struct ServeArgs {
     const GroupProblem *probs;

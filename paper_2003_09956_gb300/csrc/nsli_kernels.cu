@@ -23,6 +23,7 @@
 
 #include "nsli.h"
 #include "nsli_internal.h"
+#include "nsli_async.cuh"
 #include "nsli_sumsq.cuh"
 
 namespace nsli {
@@ -101,75 +102,7 @@ template <> __device__ __forceinline__ void decode<NSLI_FP8E4M3>(const uint4 q, 
     }
 }
 
-// ------------------------------------------------ barriers and bulk copies --
-
-__device__ __forceinline__ unsigned int smem_u32(const void *p)
-{
-    return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned int bar, unsigned int count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned int bar, unsigned int bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned int bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned int bar, unsigned int parity)
-{
-    unsigned int ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for the phase of the given parity to complete by polling (a
-// non-suspending test: the waiting warps resume as soon as the phase
-// completes).  Gives up after kWaitLimitCycles SM cycles (about two seconds
-// at the maximum clock), checked every 256 polls.  Returns true on success.
-constexpr long long kWaitLimitCycles = 4000000000ll;
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned int bar, unsigned int parity)
-{
-    const long long t0 = clock64();
-    for (unsigned int it = 0;; ++it) {
-        if (mbar_test(bar, parity))
-            return true;
-        if ((it & 255u) == 255u && clock64() - t0 > kWaitLimitCycles)
-            return false;
-    }
-}
-__device__ __forceinline__ void bulk_g2s(unsigned int dst, const void *src, unsigned int bytes,
-                                         unsigned int bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-// Block barrier (id 1) with an OR-vote, so that every thread leaves the
-// loop together when any of them gave up waiting.
-__device__ __forceinline__ int bar_all_or(int nthreads, int pred)
-{
-    unsigned int out;
-    asm volatile(
-        "{\n\t.reg .pred q, p;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(out)
-        : "r"(pred), "r"(nthreads)
-        : "memory");
-    return (int)out;
-}
+// barriers and bulk copies: nsli_async.cuh
 
 template <typename T> __device__ __forceinline__ T warp_sum(T v)
 {
@@ -751,8 +684,10 @@ __global__ void __launch_bounds__(kLongThreads, 1) map_long_kernel(const MapArgs
 // run, so the exchange latency is not on the critical path.  Eight exchange
 // buffers suffice: a CTA sends row k only after every CTA sent row k - D,
 // i.e. after every CTA finished reading rows up to k - 2D - 1, and
-// 8 >= 2D + 1.  The ring holds the rows awaiting their exchange, the row
-// being mapped and at least one prefetched row.  Every wait is bounded; all CTAs
+// 8 >= 2D + 1.  A row's stage is refilled as soon as every mapping warp has
+// finished the row (an "empty" barrier per stage that the warps arrive on
+// and the exchange warp waits for), so the ring holds the D + 1 rows in use
+// and the rest of its stages are in flight.  Every wait is bounded; all CTAs
 // of a cluster meet at a cluster barrier before they exit, so no CTA's
 // shared memory is written after it has gone.
 __device__ __forceinline__ unsigned int cluster_rank()
@@ -810,17 +745,26 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(unsigned int bar, unsi
 constexpr int kClXB = 8;        // exchange buffers (row k uses k % 8)
 constexpr int kClFull = 0;      // 8 full barriers (stages)
 constexpr int kClXbar = 64;     // 8 exchange barriers
+constexpr int kClEmpty = 128;   // 8 empty barriers (stages)
 constexpr int kClRed = 512;     // [2][16] warp sums
 constexpr int kClXch = 1024;    // [8][8] exchanged partial dots
 static_assert(kClXch + kClXB * 8 * 8 <= kSmemHeader, "cluster Map header fits");
 
+// 512 threads map; a 17th warp (the exchange warp) issues the bulk copies,
+// waits for the exchanges, adds the warps' sums and sends the partial dots,
+// so the latency of the remote stores and releases is off the mapping
+// warps' path (they only meet it at the per-row block barrier).
+constexpr int kClusterCompute = 512;
+constexpr int kClusterThreads = kClusterCompute + 32;
+
 template <int S, int VPT>
-__global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const MapArgs p)
+__global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const MapArgs p)
 {
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
     constexpr int EPV = Tr::EPV;
+    constexpr int NCW = kClusterCompute / 32;   // mapping warps
 
     DevState *st = p.st;
     if (!p.ignore_done && *(volatile int *)&st->done)
@@ -828,12 +772,14 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kClFull);
     unsigned long long *xbar = reinterpret_cast<unsigned long long *>(smem + kClXbar);
+    unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + kClEmpty);
     Acc *xch = reinterpret_cast<Acc *>(smem + kClXch);
     Acc *red = reinterpret_cast<Acc *>(smem + kClRed);
     unsigned char *stages = smem + kSmemHeader;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nwarps = (int)blockDim.x >> 5;
+    const bool xw = warp == NCW;                 // the exchange warp
+    const bool leader = xw && lane == 0;
     const int C = p.cluster;
     const unsigned int rank = cluster_rank();
     const long long cl = blockIdx.x / C;
@@ -859,8 +805,10 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
     };
 
     if (tid == 0) {
-        for (int q = 0; q < p.nstage; ++q)
+        for (int q = 0; q < p.nstage; ++q) {
             mbar_init(smem_u32(&full[q]), 1u);
+            mbar_init(smem_u32(&empty[q]), (unsigned int)NCW);
+        }
         for (int q = 0; q < kClXB; ++q)
             mbar_init(smem_u32(&xbar[q]), (unsigned int)C);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -869,7 +817,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
     __syncthreads();
     cluster_sync_all();   // every exchange barrier of the cluster is initialised
     int issued = 0;
-    if (tid == 0) {
+    if (leader) {
         const int first = nrows < p.nstage ? nrows : p.nstage;
         for (int q = 0; q < first; ++q)
             issue(q);
@@ -883,9 +831,9 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
         const Acc *xg = static_cast<const Acc *>(p.x);
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int j = tid + v * (int)blockDim.x;
+            const int j = tid + v * kClusterCompute;
             voff[v] = j * 16;
-            vok[v] = j < my_nv;
+            vok[v] = !xw && j < my_nv;
 #pragma unroll
             for (int e = 0; e < EPV; ++e) {
                 xr[v][e] = vok[v] ? xg[(v0 + j) * EPV + e] : Acc(0);
@@ -896,15 +844,14 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
     const Acc tk = (Acc)((double)st->tick * st->rho);
     long long h_loc = 0;
     Acc mv = neg_inf<Acc>(), mn = neg_inf<Acc>(), mb = Acc(0);
-    int aborted = 0, consumed = 0;
+    int aborted = 0, at = 0, stalled = 0;
 
     const int D = p.cluster_lag;
     for (int s = 0; s < nrows + D; ++s) {
         int flag = 0;
-        if (s < nrows) {
+        if (s < nrows && !xw) {
             const int stage = s % p.nstage;
             flag = mbar_wait_bounded(smem_u32(&full[stage]), (unsigned int)((s / p.nstage) & 1)) ? 0 : 1;
-            consumed = s + 1;
             const unsigned char *row = stages + (size_t)stage * p.stage_stride;
             Acc pe = Acc(0), po = Acc(0);
 #pragma unroll
@@ -921,35 +868,44 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
             if (lane == 0)
                 red[(s & 1) * 16 + warp] = ws;
         }
-        if (tid == 0 && s >= D) {
+        if (leader && s >= D) {
             const int t = s - D;
-            if (!mbar_wait_cluster_bounded(smem_u32(&xbar[t % kClXB]), (unsigned int)((t / kClXB) & 1)))
+            if (stalled || !mbar_wait_cluster_bounded(smem_u32(&xbar[t % kClXB]), (unsigned int)((t / kClXB) & 1)))
                 flag = 1;
         }
         aborted = bar_all_or((int)blockDim.x, flag);
+        at = s;
         if (aborted)
             break;
-        if (tid == 0 && s >= D + 1 && issued < nrows) {
-            // the stage of row s - D - 1, finished in the previous iteration
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(issued);
-            ++issued;
-        }
-        if (warp == 0 && s < nrows) {
-            // the warps' sums in a fixed butterfly; lane q sends this CTA's
-            // partial dot of row s to CTA q
-            Acc tot = lane < nwarps ? red[(s & 1) * 16 + lane] : Acc(0);
+        if (xw) {
+            if (s < nrows) {
+                // the mapping warps' sums in a fixed butterfly; lane q sends
+                // this CTA's partial dot of row s to CTA q
+                Acc tot = lane < NCW ? red[(s & 1) * 16 + lane] : Acc(0);
 #pragma unroll
-            for (int off = 8; off > 0; off >>= 1)
-                tot += __shfl_xor_sync(0xffffffffu, tot, off);
-            if (lane < C) {
-                const unsigned int la = smem_u32(&xch[(s % kClXB) * 8 + rank]);
-                const unsigned int lb = smem_u32(&xbar[s % kClXB]);
-                st_remote(map_to_rank(la, (unsigned int)lane), tot);
-                arrive_remote(map_to_rank(lb, (unsigned int)lane));
+                for (int off = 8; off > 0; off >>= 1)
+                    tot += __shfl_xor_sync(0xffffffffu, tot, off);
+                if (lane < C) {
+                    const unsigned int la = smem_u32(&xch[(s % kClXB) * 8 + rank]);
+                    const unsigned int lb = smem_u32(&xbar[s % kClXB]);
+                    st_remote(map_to_rank(la, (unsigned int)lane), tot);
+                    arrive_remote(map_to_rank(lb, (unsigned int)lane));
+                }
             }
-        }
-        if (s >= D) {
+            if (lane == 0 && s >= D && issued < nrows) {
+                // refill the stage of row s - D once every mapping warp has
+                // finished it (in this iteration, below)
+                const int t = s - D;
+                if (mbar_wait_bounded(smem_u32(&empty[t % p.nstage]), (unsigned int)((t / p.nstage) & 1))) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(issued);
+                    ++issued;
+                } else {
+                    atomicOr(&st->error, ERRF_TIMEOUT);   // the next barrier ends the loop
+                    stalled = 1;
+                }
+            }
+        } else if (s >= D) {
             const int t = s - D;
             Acc dot = Acc(0);
             for (int q = 0; q < C; ++q)
@@ -981,14 +937,18 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
                     }
                 }
             }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(smem_u32(&empty[t % p.nstage]));   // row t's stage is free
         }
     }
 
     if (aborted) {
         // record the error; wait (bounded) for this CTA's copies in flight
-        if (tid == 0) {
+        // (rows before the aborted iteration were waited for already)
+        if (leader) {
             atomicOr(&st->error, ERRF_TIMEOUT);
-            for (int q = consumed; q < issued; ++q)
+            for (int q = at < nrows ? at : nrows; q < issued; ++q)
                 mbar_wait_bounded(smem_u32(&full[q % p.nstage]), (unsigned int)((q / p.nstage) & 1));
         }
     } else {
@@ -996,7 +956,7 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) map_cluster_kernel(const 
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             if (vok[v]) {
-                const long long j = tid + v * (long long)blockDim.x;
+                const long long j = tid + v * (long long)kClusterCompute;
 #pragma unroll
                 for (int e = 0; e < EPV; ++e)
                     py[j * EPV + e] = yr[v][e];
@@ -1377,6 +1337,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 struct ServeShared {
     unsigned long long t_start;
     int ok, running;
+    int item;    // the work item the CTA took
 };
 constexpr int kServeSharedOffset = 2048;
 static_assert(kServeSharedOffset + sizeof(ServeShared) <= kSmemHeader, "serving words fit the ring header");
@@ -1461,6 +1422,8 @@ __device__ __forceinline__ void serve_control(const ServeArgs &a, long long roun
         *(volatile unsigned long long *)&a.ctrl->rounds = (unsigned long long)round;
         const int yield = *(volatile int *)&a.ctrl->yield;
         a.sync->stop = (yield || running == 0 || round >= a.max_rounds || now - t_start > a.max_ns) ? 1 : 0;
+        a.sync->map_next = 0u;   // every CTA has left the previous round's phases
+        a.sync->red_next = 0u;
         __threadfence_system();
     }
 }
@@ -1496,7 +1459,15 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeA
             break;
         if (*(volatile int *)&a.sync->stop)
             break;
-        for (int i = blockIdx.x; i < a.nitems; i += G) {
+        // items are taken one at a time from a shared counter (an item's
+        // arithmetic does not depend on the CTA that runs it)
+        for (;;) {
+            if (threadIdx.x == 0)
+                ss.item = (int)atomicAdd(&a.sync->map_next, 1u);
+            __syncthreads();
+            const int i = ss.item;
+            if (i >= a.nitems)
+                break;
             const GroupItem it = a.items[i];
             const GroupProblem &gp = a.probs[it.prob];
             if (!*(volatile int *)&gp.map.st->done) {
@@ -1518,7 +1489,13 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeA
         }
         if (!serve_grid_sync(a.sync, G))
             break;
-        for (int i = blockIdx.x; i < a.nreds; i += G) {
+        for (;;) {
+            if (threadIdx.x == 0)
+                ss.item = (int)atomicAdd(&a.sync->red_next, 1u);
+            __syncthreads();
+            const int i = ss.item;
+            if (i >= a.nreds)
+                break;
             const GroupRed t = a.reds[i];
             const GroupProblem &gp = a.probs[t.prob];
             reduce_body<Acc, NGRP>(gp.red, t.blk, gp.red_blocks, rsh);
@@ -1895,7 +1872,7 @@ cudaError_t cluster_prepare(int storage, int vpt, int C, size_t smem, int *clust
         return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C);
-    cfg.blockDim = dim3(kMapMaxConsumers);
+    cfg.blockDim = dim3(kClusterThreads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1917,7 +1894,7 @@ cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers
             return cudaErrorInvalidValue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(grid * a.cluster));
-        cfg.blockDim = dim3(kMapMaxConsumers);
+        cfg.blockDim = dim3(kClusterThreads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
         cudaLaunchAttribute at[1];

@@ -249,6 +249,29 @@ def test_dense_solve_iteration_count_within_one_percent(storage):
     assert res["max_viol"] <= 1e-6 * res["max_abs_b"]
 
 
+@pytest.mark.parametrize("m,n", [(2048, 256), (1024, 256)])
+def test_mid_size_solves_match_oracle_in_binary32_and_bf16(m, n):
+    """A stationary dense system drawn on the bf16 grid (so binary32 and
+    bf16 storage hold the same values) solved from x0 ~ N(0, 25 I) to the
+    binary64-confirmed stop max r_i <= 1e-6 max|b|: both storages end
+    within 1 % of the oracle's iteration count (about 10^4 iterations),
+    with the oracle's binary64 violation at the device's final iterate
+    below the threshold."""
+    p = workloads.dense_system(m, n, seed=5000 + n + m, grid="bf16")
+    ref = oracle.solve(p["A"], p["b0"], p["x0"], stop=oracle.STOP_MAXVIOL_REL, eps=1e-6, max_iter=2000000)
+    assert ref["status"] == oracle.OK
+    n2, _ = oracle.norms2(p["A"])
+    for storage in ("f32", "bf16"):
+        with nsli.Solver(p["A"], p["b0"], p["x0"], storage=storage) as s:
+            res = s.solve(stop="maxviol_rel", eps=1e-6, max_iter=2000000, block_iters=256)
+            xg = s.get_x()
+        assert res["status"] == nsli.OK
+        assert abs(res["iters"] - ref["iters"]) <= max(2, 0.01 * ref["iters"]), (storage, res["iters"], ref["iters"])
+        mr = oracle.map_reduce(p["A"], p["b0"], n2, xg)
+        assert mr["maxviol"] <= 1e-6 * mr["maxb"], (storage, mr["maxviol"], mr["maxb"])
+        assert res["max_viol"] == pytest.approx(mr["maxviol"], rel=1e-9, abs=1e-12 * mr["maxb"])
+
+
 def test_strictly_feasible_start_gpu():
     p = workloads.dense_system(800, 64, seed=3)
     for storage in STORAGES:
@@ -417,7 +440,8 @@ def test_long_rows_every_group_size(monkeypatch, budget_mb, storage, m, n):
     test_long_rows_one_step_and_trajectory(storage, m, n)
 
 
-@pytest.mark.parametrize("storage,m,n", [("f32", 200, 54000), ("bf16", 300, 40000), ("f64", 200, 9000)])
+@pytest.mark.parametrize("storage,m,n", [("f32", 200, 54000), ("bf16", 300, 40000), ("f64", 200, 9000),
+                                         ("fp8", 200, 70000)])
 def test_long_rows_two_pass_kernel(monkeypatch, storage, m, n):
     """The two-pass kernel (NSLI_LONG_CLUSTER=0) keeps the same parity bar."""
     monkeypatch.setenv("NSLI_LONG_CLUSTER", "0")
@@ -427,8 +451,8 @@ def test_long_rows_two_pass_kernel(monkeypatch, storage, m, n):
 @pytest.mark.parametrize("storage,m,n,size", [("bf16", 300, 40000, "4"), ("fp8", 200, 70000, "8"),
                                              ("f32", 400, 60000, "8"), ("f64", 200, 9000, "4")])
 def test_long_rows_cluster_kernel_every_storage_and_size(monkeypatch, storage, m, n, size):
-    """The cluster kernel forced on (bf16 / fp8 use the two-pass kernel by
-    default) and at other cluster sizes: same parity bar."""
+    """The cluster kernel at cluster sizes other than the default choice:
+    same parity bar."""
     monkeypatch.setenv("NSLI_LONG_CLUSTER", "1")
     monkeypatch.setenv("NSLI_LONG_CLUSTER_SIZE", size)
     test_long_rows_one_step_and_trajectory(storage, m, n)
