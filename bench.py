@@ -142,12 +142,15 @@ MAP_SOURCE_END = "// --------------------------------------------------- Map, lo
 
 
 def kernels_sha():
-    """Hash of the source the Map kernel is compiled from: nsli_kernels.cu up
-    to the long-row section (helpers, the Map body and its kernels; the
-    kernels after it do not enter the Map)."""
-    src = open(os.path.join(ROOT, "paper_2003_09956_gb300", "csrc", "nsli_kernels.cu")).read()
+    """Hash of the source the Map kernel is compiled from: its barrier and
+    bulk-copy helpers (nsli_async.cuh) and nsli_kernels.cu up to the
+    long-row section (helpers, the Map body and its kernels; the kernels
+    after it do not enter the Map)."""
+    csrc = os.path.join(ROOT, "paper_2003_09956_gb300", "csrc")
+    helpers = open(os.path.join(csrc, "nsli_async.cuh")).read()
+    src = open(os.path.join(csrc, "nsli_kernels.cu")).read()
     end = src.find(MAP_SOURCE_END)
-    return hashlib.sha256(src[:end if end >= 0 else len(src)].encode()).hexdigest()[:12]
+    return hashlib.sha256((helpers + src[:end if end >= 0 else len(src)]).encode()).hexdigest()[:12]
 
 
 def profiled_traffic(workload, storage):

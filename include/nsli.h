@@ -315,7 +315,7 @@ int nsli_shard_step(nsli_handle h, const double *records, int32_t nranks, int32_
  * inside the library, held by every GPU that loads it until the process
  * exits; n larger than 2^20 is rejected with NSLI_ERR_UNSUPPORTED.  The
  * first call on a device looks up that array's device address (once per
- * device), so make it before any stream capture.  All calls share the
+ * device).  All calls share the
  * array and each call clears the part it accumulates into: calls that
  * overlap on the GPU race and must not be issued.  Calls no cudaMalloc or
  * cudaFree.  A CUDA error already pending when the call starts is left in

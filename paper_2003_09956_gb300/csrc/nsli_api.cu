@@ -39,7 +39,7 @@ struct nsli_solver {
     long long m = 0, n = 0, ld = 0;
     int elem_bytes = 4, epv = 4, row_bytes = 0, nv = 0;
     int vpt = 1, consumers = 32, R = 1, nstage = 2, stage_stride = 0;
-    int cluster = 0, slice_nv = 0, cluster_vpt = 0, cluster_lag = 1;   // long rows on thread-block clusters
+    int cluster = 0, slice_nv = 0, cluster_vpt = 0, cluster_lag = 1, cluster_rg = 1;   // long rows on clusters
     bool guard = true;
     size_t smem = 0;
     int G = 1, red_grid = 1, num_sms = 1;
@@ -207,16 +207,32 @@ int choose_config(nsli_solver *h)
                 int cv = 1;
                 while ((long long)cv * kMapMaxConsumers < slice)
                     cv *= 2;
+                // rows per block barrier: two for bf16 / FP8 (short row
+                // slices, whose per-row fixed cost dominates) where the
+                // ring holds the groups in use and one more
+                // (NSLI_LONG_CLUSTER_RG forces 1 or 2)
+                int rg = ((h->storage == NSLI_BF16 || h->storage == NSLI_FP8E4M3) && ns >= 6) ? 2 : 1;
+                if (const char *rs = std::getenv("NSLI_LONG_CLUSTER_RG")) {
+                    const int v = std::atoi(rs);
+                    if (v == 1 || (v == 2 && ns >= 6 && h->storage != NSLI_F64 && h->storage != NSLI_F32))
+                        rg = v;
+                }
                 int clusters = 0;
                 const size_t smem = (size_t)kSmemHeader + (size_t)ns * stride;
-                if (cluster_prepare(h->storage, cv, C, smem, &clusters) == cudaSuccess && clusters > 0) {
+                if (cluster_prepare(h->storage, cv, rg, C, smem, &clusters) == cudaSuccess && clusters > 0) {
                     h->cluster = C;
                     h->slice_nv = slice;
                     h->cluster_vpt = cv;
-                    h->cluster_lag = std::max(1, std::min(3, ns - 3));
+                    h->cluster_rg = rg;
+                    // groups between a group's Map and the wait for its
+                    // exchange: the ring holds D + 1 groups in use and at
+                    // least one prefetched (measured best: 2 at four
+                    // binary32 stages)
+                    const int ng = ns / rg;
+                    h->cluster_lag = std::max(1, std::min(rg == 1 ? 2 : 1, ng - 2));
                     if (const char *ls = std::getenv("NSLI_LONG_CLUSTER_LAG")) {
-                        const int v = std::atoi(ls);   // 1..3, leaving a stage to prefetch
-                        if (v >= 1 && v <= 3 && v <= ns - 2)
+                        const int v = std::atoi(ls);   // 1..3, leaving a group to prefetch
+                        if (v >= 1 && v <= 3 && v <= ng - 2)
                             h->cluster_lag = v;
                     }
                     h->consumers = kMapMaxConsumers;
@@ -309,6 +325,7 @@ MapArgs map_args(nsli_solver *h)
     a.slice_nv = h->slice_nv;
     a.cluster_vpt = h->cluster_vpt;
     a.cluster_lag = h->cluster_lag;
+    a.cluster_rg = h->cluster_rg;
     return a;
 }
 
@@ -406,6 +423,8 @@ int read_flags(nsli_solver *h)
     CK(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
     const int f = *h->flags_host;
+    if (f & PREPF_TIMEOUT)
+        return set_err(h, NSLI_ERR_TIMEOUT, "a row copy did not arrive within the wait limit");
     if (f & PREPF_NONFINITE)
         return set_err(h, NSLI_ERR_NONFINITE, "NaN or Inf in the input");
     if (f & PREPF_ZERO_ROW)

@@ -68,7 +68,7 @@ __host__ __device__ __forceinline__ bool step_norm_below(double dx2, double eps)
 
 enum : int { ST_RUNNING = 2, ST_CANDIDATE = 3 };   // reported as NSLI_RUNNING / NSLI_CANDIDATE
 enum : int { ERRF_TIMEOUT = 1 };
-enum : int { PREPF_ZERO_ROW = 1, PREPF_NONFINITE = 2 };
+enum : int { PREPF_ZERO_ROW = 1, PREPF_NONFINITE = 2, PREPF_TIMEOUT = 4 };
 
 // Result of the binary64 check: maxima kept as order-preserving integers.
 struct VerOut {
@@ -97,7 +97,8 @@ struct MapArgs {
     int cluster;           // long rows on thread-block clusters: CTAs per cluster (0: not used)
     int slice_nv;          // ... 16-byte vectors of a row per CTA of a cluster
     int cluster_vpt;       // ... vectors per thread (instance of the cluster kernel)
-    int cluster_lag;       // ... rows between a row's Map and the wait for its exchange (1..3)
+    int cluster_lag;       // ... row groups between a group's Map and the wait for its exchange (1..3)
+    int cluster_rg;        // ... rows per group (1, or 2 for bf16 / FP8)
 };
 
 struct ReduceArgs {
@@ -199,7 +200,7 @@ cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers
                        cudaStream_t s, const MapArgs &a);
 // long rows on clusters of C CTAs: set the kernel's shared memory and return
 // how many clusters can be resident at once (0: the shape does not fit)
-cudaError_t cluster_prepare(int storage, int vpt, int C, size_t smem, int *clusters);
+cudaError_t cluster_prepare(int storage, int vpt, int rg, int C, size_t smem, int *clusters);
 cudaError_t reduce_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a);
 cudaError_t reduce_only_launch(bool f64, int grid, cudaStream_t s, const ReduceArgs &a,
                                double *y_out);

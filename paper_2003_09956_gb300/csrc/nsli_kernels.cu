@@ -742,24 +742,31 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(unsigned int bar, unsi
 }
 
 // shared-memory header of the cluster Map (within kSmemHeader)
-constexpr int kClXB = 8;        // exchange buffers (row k uses k % 8)
+constexpr int kClXB = 8;        // exchange buffers (group k uses k % 8)
 constexpr int kClFull = 0;      // 8 full barriers (stages)
 constexpr int kClXbar = 64;     // 8 exchange barriers
 constexpr int kClEmpty = 128;   // 8 empty barriers (stages)
-constexpr int kClRed = 512;     // [2][16] warp sums
-constexpr int kClXch = 1024;    // [8][8] exchanged partial dots
-static_assert(kClXch + kClXB * 8 * 8 <= kSmemHeader, "cluster Map header fits");
+constexpr int kClRed = 512;     // [2][2][16] warp sums
+constexpr int kClXch = 1024;    // [8][2][8] exchanged partial dots
+static_assert(kClRed + 2 * 2 * 16 * 8 <= kClXch, "cluster Map warp sums fit");
+static_assert(kClXch + kClXB * 2 * 8 * 8 <= kSmemHeader, "cluster Map header fits");
 
 // 512 threads map; a 17th warp (the exchange warp) issues the bulk copies,
 // waits for the exchanges, adds the warps' sums and sends the partial dots,
 // so the latency of the remote stores and releases is off the mapping
-// warps' path (they only meet it at the per-row block barrier).
+// warps' path (they only meet it at the per-group block barrier).
 constexpr int kClusterCompute = 512;
 constexpr int kClusterThreads = kClusterCompute + 32;
 
-template <int S, int VPT>
+// RG = rows per group (1 or 2): the rows of a group share one block barrier
+// and one exchange message, and their dependent chains interleave.  The
+// arithmetic of every row is the same for both (the warp fold of two rows
+// adds the same operands in the same tree as one warp butterfly per row,
+// and rows enter y in row order).
+template <int S, int VPT, int RG>
 __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const MapArgs p)
 {
+    static_assert(RG == 1 || RG == 2, "one or two rows per group");
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
@@ -773,8 +780,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kClFull);
     unsigned long long *xbar = reinterpret_cast<unsigned long long *>(smem + kClXbar);
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem + kClEmpty);
-    Acc *xch = reinterpret_cast<Acc *>(smem + kClXch);
-    Acc *red = reinterpret_cast<Acc *>(smem + kClRed);
+    Acc *xch = reinterpret_cast<Acc *>(smem + kClXch);   // [group % 8][row][rank]
+    Acc *red = reinterpret_cast<Acc *>(smem + kClRed);   // [group & 1][row][warp]
     unsigned char *stages = smem + kSmemHeader;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -786,6 +793,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
     const long long row_begin = cl * p.rows_base + (cl < p.rows_rem ? cl : (long long)p.rows_rem);
     const long long row_end = row_begin + p.rows_base + (cl < p.rows_rem ? 1 : 0);
     const int nrows = (int)(row_end - row_begin);
+    const int ngroups = (nrows + RG - 1) / RG;
     const long long v0 = (long long)rank * p.slice_nv;
     const int my_nv = (int)max(0ll, min((long long)p.slice_nv, (long long)p.nv - v0));
     const unsigned int slice_bytes = (unsigned int)my_nv * 16u;
@@ -793,7 +801,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
     const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
     const unsigned char *Mb = static_cast<const unsigned char *>(p.meta);
 
-    auto issue = [&](int s) {
+    auto issue = [&](int s) {   // row s of the block into its stage
         const int stage = s % p.nstage;
         const long long row = row_begin + s;
         unsigned char *dst = stages + (size_t)stage * p.stage_stride;
@@ -847,108 +855,137 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
     int aborted = 0, at = 0, stalled = 0;
 
     const int D = p.cluster_lag;
-    for (int s = 0; s < nrows + D; ++s) {
+    for (int g = 0; g < ngroups + D; ++g) {
         int flag = 0;
-        if (s < nrows && !xw) {
-            const int stage = s % p.nstage;
-            flag = mbar_wait_bounded(smem_u32(&full[stage]), (unsigned int)((s / p.nstage) & 1)) ? 0 : 1;
-            const unsigned char *row = stages + (size_t)stage * p.stage_stride;
-            Acc pe = Acc(0), po = Acc(0);
+        if (g < ngroups && !xw) {
+            // partial dots of the group's rows (a missing second row adds 0)
+            Acc acc[RG];
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                if (vok[v] && !flag) {
-                    Acc a[EPV];
-                    decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+            for (int rr = 0; rr < RG; ++rr) {
+                const int s = g * RG + rr;
+                Acc pe = Acc(0), po = Acc(0);
+                if (s < nrows) {
+                    const int stage = s % p.nstage;
+                    if (!mbar_wait_bounded(smem_u32(&full[stage]), (unsigned int)((s / p.nstage) & 1)))
+                        flag = 1;
+                    const unsigned char *row = stages + (size_t)stage * p.stage_stride;
 #pragma unroll
-                    for (int e = 0; e < EPV; e += 2)
-                        fma2(pe, po, a[e], a[e + 1], xr[v][e], xr[v][e + 1]);
+                    for (int v = 0; v < VPT; ++v) {
+                        if (vok[v] && !flag) {
+                            Acc a[EPV];
+                            decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+#pragma unroll
+                            for (int e = 0; e < EPV; e += 2)
+                                fma2(pe, po, a[e], a[e + 1], xr[v][e], xr[v][e + 1]);
+                        }
+                    }
                 }
+                acc[rr] = pe + po;
             }
-            const Acc ws = warp_sum(pe + po);
-            if (lane == 0)
-                red[(s & 1) * 16 + warp] = ws;
+            const Acc ws = warp_fold_rows<RG>(acc, lane);   // lanes [16q, 16q + 16) end with row q
+            if ((lane & (32 / RG - 1)) == 0)
+                red[(g & 1) * 32 + (lane / (32 / RG)) * 16 + warp] = ws;
         }
-        if (leader && s >= D) {
-            const int t = s - D;
+        if (leader && g >= D) {
+            const int t = g - D;
             if (stalled || !mbar_wait_cluster_bounded(smem_u32(&xbar[t % kClXB]), (unsigned int)((t / kClXB) & 1)))
                 flag = 1;
         }
         aborted = bar_all_or((int)blockDim.x, flag);
-        at = s;
+        at = g;
         if (aborted)
             break;
         if (xw) {
-            if (s < nrows) {
-                // the mapping warps' sums in a fixed butterfly; lane q sends
-                // this CTA's partial dot of row s to CTA q
-                Acc tot = lane < NCW ? red[(s & 1) * 16 + lane] : Acc(0);
+            if (g < ngroups) {
+                // the mapping warps' sums in a fixed butterfly (row q in
+                // lanes [16q, 16q + 16)); lane q sends this CTA's partial
+                // dots of the group to CTA q
+                Acc tot = (RG == 2 || lane < NCW) ? red[(g & 1) * 32 + lane] : Acc(0);
 #pragma unroll
                 for (int off = 8; off > 0; off >>= 1)
                     tot += __shfl_xor_sync(0xffffffffu, tot, off);
+                Acc t1 = Acc(0);
+                if constexpr (RG == 2)
+                    t1 = __shfl_sync(0xffffffffu, tot, 16);
                 if (lane < C) {
-                    const unsigned int la = smem_u32(&xch[(s % kClXB) * 8 + rank]);
-                    const unsigned int lb = smem_u32(&xbar[s % kClXB]);
+                    const unsigned int la = smem_u32(&xch[(g % kClXB) * 16 + rank]);
+                    const unsigned int lb = smem_u32(&xbar[g % kClXB]);
                     st_remote(map_to_rank(la, (unsigned int)lane), tot);
+                    if constexpr (RG == 2)
+                        st_remote(map_to_rank(la + 8u * (unsigned int)sizeof(Acc), (unsigned int)lane), t1);
                     arrive_remote(map_to_rank(lb, (unsigned int)lane));
                 }
             }
-            if (lane == 0 && s >= D && issued < nrows) {
-                // refill the stage of row s - D once every mapping warp has
-                // finished it (in this iteration, below)
-                const int t = s - D;
-                if (mbar_wait_bounded(smem_u32(&empty[t % p.nstage]), (unsigned int)((t / p.nstage) & 1))) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(issued);
-                    ++issued;
-                } else {
-                    atomicOr(&st->error, ERRF_TIMEOUT);   // the next barrier ends the loop
-                    stalled = 1;
-                }
-            }
-        } else if (s >= D) {
-            const int t = s - D;
-            Acc dot = Acc(0);
-            for (int q = 0; q < C; ++q)
-                dot += xch[(t % kClXB) * 8 + q];
-            const unsigned char *row = stages + (size_t)(t % p.nstage) * p.stage_stride;
-            const Meta md = *reinterpret_cast<const Meta *>(row + meta_off);
-            const Acc sc = (Acc)meta_scale(md);
-            const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
-            const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
-            const bool viol = ri > Acc(0);
-            const Acc c = viol ? ((S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2) : Acc(0);
-            if (warp == 0) {
-                h_loc += viol ? 1 : 0;
-                mv = ri > mv ? ri : mv;
-                const Acc rn = ri * (Acc)md.inv_n;
-                mn = rn > mn ? rn : mn;
-                const Acc ab = bi < Acc(0) ? -bi : bi;
-                mb = ab > mb ? ab : mb;
-            }
-            if (c != Acc(0)) {
-#pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    if (vok[v]) {
-                        Acc a[EPV];
-                        decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
-#pragma unroll
-                        for (int e = 0; e < EPV; e += 2)
-                            fma2(yr[v][e], yr[v][e + 1], c, c, a[e], a[e + 1]);
+            if (lane == 0 && g >= D) {
+                // refill the stages of group g - D once every mapping warp
+                // has finished it (in this iteration, below)
+                const int t = g - D;
+                for (int rr = 0; rr < RG && !stalled; ++rr) {
+                    const int r = t * RG + rr;
+                    if (r >= nrows || issued >= nrows)
+                        break;
+                    if (mbar_wait_bounded(smem_u32(&empty[r % p.nstage]), (unsigned int)((r / p.nstage) & 1))) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(issued);
+                        ++issued;
+                    } else {
+                        atomicOr(&st->error, ERRF_TIMEOUT);   // the next barrier ends the loop
+                        stalled = 1;
                     }
                 }
             }
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(smem_u32(&empty[t % p.nstage]));   // row t's stage is free
+        } else if (g >= D) {
+            const int t = g - D;
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                const int r = t * RG + rr;
+                if (r >= nrows)
+                    break;
+                Acc dot = Acc(0);
+                for (int q = 0; q < C; ++q)
+                    dot += xch[(t % kClXB) * 16 + rr * 8 + q];
+                const unsigned char *row = stages + (size_t)(r % p.nstage) * p.stage_stride;
+                const Meta md = *reinterpret_cast<const Meta *>(row + meta_off);
+                const Acc sc = (Acc)meta_scale(md);
+                const Acc bi = fma(tk, (Acc)md.av, (Acc)md.b0);
+                const Acc ri = (S == NSLI_FP8E4M3) ? dot * sc - bi : dot - bi;
+                const bool viol = ri > Acc(0);
+                const Acc c = viol ? ((S == NSLI_FP8E4M3) ? ri * (Acc)md.inv_n2 * sc : ri * (Acc)md.inv_n2)
+                                   : Acc(0);
+                if (warp == 0) {
+                    h_loc += viol ? 1 : 0;
+                    mv = ri > mv ? ri : mv;
+                    const Acc rn = ri * (Acc)md.inv_n;
+                    mn = rn > mn ? rn : mn;
+                    const Acc ab = bi < Acc(0) ? -bi : bi;
+                    mb = ab > mb ? ab : mb;
+                }
+                if (c != Acc(0)) {
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        if (vok[v]) {
+                            Acc a[EPV];
+                            decode<S>(*reinterpret_cast<const uint4 *>(row + voff[v]), a);
+#pragma unroll
+                            for (int e = 0; e < EPV; e += 2)
+                                fma2(yr[v][e], yr[v][e + 1], c, c, a[e], a[e + 1]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&empty[r % p.nstage]));   // row r's stage is free
+            }
         }
     }
 
     if (aborted) {
         // record the error; wait (bounded) for this CTA's copies in flight
-        // (rows before the aborted iteration were waited for already)
+        // (rows before the aborted group were waited for already)
         if (leader) {
             atomicOr(&st->error, ERRF_TIMEOUT);
-            for (int q = at < nrows ? at : nrows; q < issued; ++q)
+            const int first = at * RG < nrows ? at * RG : nrows;
+            for (int q = first; q < issued; ++q)
                 mbar_wait_bounded(smem_u32(&full[q % p.nstage]), (unsigned int)((q / p.nstage) & 1));
         }
     } else {
@@ -978,31 +1015,44 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
 // instances up to the register-resident limit of the storage type (8, 8,
 // 4, 2 vectors per thread for binary64, binary32, bf16, fp8)
 template <int S> constexpr int cluster_vpt_max() { return S == NSLI_BF16 ? 4 : (S == NSLI_FP8E4M3 ? 2 : 8); }
-template <int S> const void *cluster_fn_s(int vpt)
+// two rows per group for the storage types with short row slices (bf16,
+// FP8); binary64 and binary32 take one
+template <int S> constexpr int cluster_rg_max() { return (S == NSLI_BF16 || S == NSLI_FP8E4M3) ? 2 : 1; }
+template <int S, int RG> const void *cluster_fn_v(int vpt)
 {
     if (vpt == 1)
-        return (const void *)map_cluster_kernel<S, 1>;
+        return (const void *)map_cluster_kernel<S, 1, RG>;
     if (vpt == 2)
-        return (const void *)map_cluster_kernel<S, 2>;
+        return (const void *)map_cluster_kernel<S, 2, RG>;
     if constexpr (cluster_vpt_max<S>() >= 4) {
         if (vpt == 4)
-            return (const void *)map_cluster_kernel<S, 4>;
+            return (const void *)map_cluster_kernel<S, 4, RG>;
     }
     if constexpr (cluster_vpt_max<S>() >= 8) {
         if (vpt == 8)
-            return (const void *)map_cluster_kernel<S, 8>;
+            return (const void *)map_cluster_kernel<S, 8, RG>;
     }
     return nullptr;
 }
-const void *cluster_fn(int storage, int vpt)
+template <int S> const void *cluster_fn_s(int vpt, int rg)
+{
+    if (rg == 1)
+        return cluster_fn_v<S, 1>(vpt);
+    if constexpr (cluster_rg_max<S>() >= 2) {
+        if (rg == 2)
+            return cluster_fn_v<S, 2>(vpt);
+    }
+    return nullptr;
+}
+const void *cluster_fn(int storage, int vpt, int rg)
 {
     if (vpt > map_vpt_limit(storage))
         return nullptr;
     switch (storage) {
-    case NSLI_F64: return cluster_fn_s<NSLI_F64>(vpt);
-    case NSLI_F32: return cluster_fn_s<NSLI_F32>(vpt);
-    case NSLI_BF16: return cluster_fn_s<NSLI_BF16>(vpt);
-    case NSLI_FP8E4M3: return cluster_fn_s<NSLI_FP8E4M3>(vpt);
+    case NSLI_F64: return cluster_fn_s<NSLI_F64>(vpt, rg);
+    case NSLI_F32: return cluster_fn_s<NSLI_F32>(vpt, rg);
+    case NSLI_BF16: return cluster_fn_s<NSLI_BF16>(vpt, rg);
+    case NSLI_FP8E4M3: return cluster_fn_s<NSLI_FP8E4M3>(vpt, rg);
     default: return nullptr;
     }
 }
@@ -1861,10 +1911,10 @@ cudaError_t map_prepare(int storage, int vpt, bool guard, size_t smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t cluster_prepare(int storage, int vpt, int C, size_t smem, int *clusters)
+cudaError_t cluster_prepare(int storage, int vpt, int rg, int C, size_t smem, int *clusters)
 {
     *clusters = 0;
-    const void *fn = cluster_fn(storage, vpt);
+    const void *fn = cluster_fn(storage, vpt, rg);
     if (!fn || C < 2 || C > 8)
         return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1889,7 +1939,7 @@ cudaError_t map_launch(int storage, int vpt, bool guard, int grid, int consumers
 {
     if (vpt == 0 && a.cluster > 1) {
         // long rows on clusters: `grid` clusters of a.cluster CTAs
-        const void *fn = cluster_fn(storage, a.cluster_vpt);
+        const void *fn = cluster_fn(storage, a.cluster_vpt, a.cluster_rg);
         if (!fn)
             return cudaErrorInvalidValue;
         cudaLaunchConfig_t cfg = {};

@@ -4,20 +4,27 @@
 //
 // One block per updated row.  Pass 1 reads the new row (binary32 or
 // binary64 source), takes the FP8 row scale where needed, and sums the
-// squares of the values as they will be STORED, in binary64, in the same
-// order as the set-up kernel (so a row gets the same norm whether it came
-// with nsli_create or with an update).  A row that is not finite or is all
-// zeros is left as it was and flagged; otherwise pass 2 (the row is in L2
-// by then) writes the stored values, its norm, the new b0 if one was given,
-// and the row record.
+// squares of the values as they will be STORED, in the same order and
+// arithmetic as the set-up kernel (so a row gets the same norm whether it
+// came with nsli_create or with an update).  A row that is not finite or is
+// all zeros is left as it was and flagged; otherwise pass 2 writes the
+// stored values, its norm, the new b0 if one was given, and the row record.
+// Where the source row fits in shared memory and is 16-byte aligned, one
+// bulk copy stages it there first, so both passes read it from shared
+// memory (A's source is read from HBM once, and no thread waits on a
+// global load); otherwise both passes read global memory and pass 2 finds
+// the row in L2.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include <cmath>
+#include <cstdint>
+#include <cstdlib>
 
 #include "nsli.h"
 #include "nsli_internal.h"
+#include "nsli_async.cuh"
 #include "nsli_sumsq.cuh"
 
 namespace nsli {
@@ -26,7 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;   // independent loads per thread per step
 
-template <int S> __device__ __forceinline__ double stored_value(const void *src, bool f64src, long long j,
+template <int S, typename I> __device__ __forceinline__ double stored_value(const void *src, bool f64src, I j,
                                                                 float inv_scale, float scale, bool *bad)
 {
     if (S == NSLI_F64) {
@@ -64,7 +71,7 @@ template <int S> __device__ __forceinline__ double stored_value(const void *src,
 
 // The stored value of a binary32 / bf16 / FP8 row as the binary32 number it
 // is (no binary64 conversion).
-template <int S> __device__ __forceinline__ float stored_value_f(const void *src, bool f64src, long long j,
+template <int S, typename I> __device__ __forceinline__ float stored_value_f(const void *src, bool f64src, I j,
                                                                  float inv_scale, float scale, bool *bad)
 {
     if (S == NSLI_F32) {
@@ -95,8 +102,8 @@ template <int S> __device__ __forceinline__ float stored_value_f(const void *src
     }
 }
 
-template <int S> __device__ __forceinline__ void store_value(void *A, long long at, const void *src, bool f64src,
-                                                             long long j, bool in, float inv_scale)
+template <int S, typename I> __device__ __forceinline__ void store_value(void *A, I at, const void *src, bool f64src,
+                                                                         I j, bool in, float inv_scale)
 {
     if (S == NSLI_F64) {
         const double v = in ? (f64src ? static_cast<const double *>(src)[j]
@@ -118,11 +125,85 @@ template <int S> __device__ __forceinline__ void store_value(void *A, long long 
     }
 }
 
-template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(const UpdateArgs p)
+template <int S> __host__ __device__ constexpr int stored_bytes() { return S == NSLI_F64 ? 8 : (S == NSLI_F32 ? 4 : (S == NSLI_BF16 ? 2 : 1)); }
+
+// Pass 2 of a row staged in shared memory: 16-byte vectors of the stored
+// row, vector q holding elements [qW, qW + W) (W = 16 / stored bytes),
+// zeros past n; the conversions are those of store_value, two elements per
+// instruction for bf16 (the same rounding, element by element).  Binary64,
+// binary32 and bf16 storage.
+template <int S> __device__ __forceinline__ void store_row_vec(void *Arow, const unsigned char *src, bool f64src,
+                                                               int n, int ld)
 {
-    const long long r = blockIdx.x;
-    if (r >= p.rows)
-        return;
+    static_assert(S != NSLI_FP8E4M3, "FP8 rows are updated from global memory");
+    constexpr int W = 16 / stored_bytes<S>();
+    const int nvec = ld / W;   // rows are padded to whole 16-byte vectors
+    uint4 *dst = static_cast<uint4 *>(Arow);
+    for (int q = threadIdx.x; q < nvec; q += kThreads) {
+        const int j0 = q * W;
+        float f[8];
+        double d[2];
+        if (S == NSLI_F64) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int j = j0 + e;
+                d[e] = j < n ? (f64src ? reinterpret_cast<const double *>(src)[j]
+                                       : (double)reinterpret_cast<const float *>(src)[j])
+                             : 0.0;
+            }
+            uint4 o;
+            o.x = (unsigned int)__double_as_longlong(d[0]);
+            o.y = (unsigned int)((unsigned long long)__double_as_longlong(d[0]) >> 32);
+            o.z = (unsigned int)__double_as_longlong(d[1]);
+            o.w = (unsigned int)((unsigned long long)__double_as_longlong(d[1]) >> 32);
+            dst[q] = o;
+            continue;
+        }
+        if (j0 + W <= n && !(S == NSLI_F32 && f64src)) {
+            const float4 *v = reinterpret_cast<const float4 *>(src) + j0 / 4;
+#pragma unroll
+            for (int k = 0; k < W / 4; ++k) {
+                const float4 t = v[k];
+                f[4 * k] = t.x;
+                f[4 * k + 1] = t.y;
+                f[4 * k + 2] = t.z;
+                f[4 * k + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const int j = j0 + e;
+                f[e] = j < n ? (f64src ? __double2float_rn(reinterpret_cast<const double *>(src)[j])
+                                       : reinterpret_cast<const float *>(src)[j])
+                             : 0.0f;
+            }
+        }
+        uint4 o;
+        unsigned int w[4];
+        if (S == NSLI_F32) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                w[k] = __float_as_uint(f[k]);
+        } else if (S == NSLI_BF16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);   // low half: first
+                w[k] = *reinterpret_cast<const unsigned int *>(&b2);
+            }
+        }
+        o.x = w[0];
+        o.y = w[1];
+        o.z = w[2];
+        o.w = w[3];
+        dst[q] = o;
+    }
+}
+
+// The update of row r from its source row `src` (global or shared memory),
+// indices of type I within the row.
+template <int S, typename I, bool VEC> __device__ __forceinline__ void update_row(const UpdateArgs &p, long long r,
+                                                                                  const void *src)
+{
     const long long gi = p.row0 + r;
     __shared__ double sred[kThreads / 32];
     __shared__ float samax[kThreads / 32];
@@ -131,19 +212,19 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     if (threadIdx.x == 0)
         sbad = 0;
     __syncthreads();
-    const size_t eb = p.src_f64 ? 8 : 4;
-    const void *src = static_cast<const unsigned char *>(p.src) + (size_t)r * p.lda * eb;
+    const I n = (I)p.n, ld = (I)p.ld;
+    const bool f64src = p.src_f64 != 0;
     bool bad = false;
 
     float scale = 1.0f, inv_scale = 1.0f;
     if (S == NSLI_FP8E4M3) {
         float amax = 0.0f;
-        for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
+        for (I j0 = threadIdx.x; j0 < n; j0 += (I)kThreads * kUnroll) {
             float a[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                const long long j = j0 + (long long)u * kThreads;
-                a[u] = j < p.n ? fabsf(static_cast<const float *>(src)[j]) : 0.0f;
+                const I j = j0 + (I)u * kThreads;
+                a[u] = j < n ? fabsf(static_cast<const float *>(src)[j]) : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
@@ -174,13 +255,13 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     // nsli_sumsq.cuh folded only at the end); kUnroll loads in flight
     double n2 = 0.0;
     SumSq sq = sumsq_init();
-    for (long long j0 = threadIdx.x; j0 < p.n; j0 += (long long)kThreads * kUnroll) {
+    for (I j0 = threadIdx.x; j0 < n; j0 += (I)kThreads * kUnroll) {
         if constexpr (S == NSLI_F64) {
             double v[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                const long long j = j0 + (long long)u * kThreads;
-                v[u] = j < p.n ? stored_value<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0;
+                const I j = j0 + (I)u * kThreads;
+                v[u] = j < n ? stored_value<S>(src, f64src, j, inv_scale, scale, &bad) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
@@ -189,8 +270,8 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
             float v[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                const long long j = j0 + (long long)u * kThreads;
-                v[u] = j < p.n ? stored_value_f<S>(src, p.src_f64 != 0, j, inv_scale, scale, &bad) : 0.0f;
+                const I j = j0 + (I)u * kThreads;
+                v[u] = j < n ? stored_value_f<S>(src, f64src, j, inv_scale, scale, &bad) : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
@@ -224,12 +305,16 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
     }
 
     // pass 2: store (zero padding up to ld), then the row's norm and record
-    for (long long j0 = threadIdx.x; j0 < p.ld; j0 += (long long)kThreads * kUnroll) {
+    void *Arow = static_cast<unsigned char *>(p.A) + (size_t)gi * (size_t)p.ld * stored_bytes<S>();
+    if constexpr (VEC)
+        store_row_vec<S>(Arow, static_cast<const unsigned char *>(src), f64src, (int)n, (int)ld);
+    else
+    for (I j0 = threadIdx.x; j0 < ld; j0 += (I)kThreads * kUnroll) {
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const long long j = j0 + (long long)u * kThreads;
-            if (j < p.ld)
-                store_value<S>(p.A, gi * p.ld + j, src, p.src_f64 != 0, j, j < p.n, inv_scale);
+            const I j = j0 + (I)u * kThreads;
+            if (j < ld)
+                store_value<S>(Arow, j, src, f64src, j, j < n, inv_scale);
         }
     }
     if (threadIdx.x == 0) {
@@ -251,6 +336,52 @@ template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(
             static_cast<RowMeta32 *>(p.meta)[gi] = m;
         }
     }
+}
+
+// Rows read from global memory (pass 2 finds them in L2).
+template <int S> __global__ void __launch_bounds__(kThreads) update_rows_kernel(const UpdateArgs p)
+{
+    const long long r = blockIdx.x;
+    if (r >= p.rows)
+        return;
+    const size_t eb = p.src_f64 ? 8 : 4;
+    update_row<S, long long, false>(p, r, static_cast<const unsigned char *>(p.src) + (size_t)r * (size_t)p.lda * eb);
+}
+
+// Rows staged in shared memory by one bulk copy (the source row 16-byte
+// aligned; the last n * eb mod 16 bytes by plain loads).  A copy that does
+// not arrive within the wait limit leaves the row as it was and sets
+// PREPF_TIMEOUT; the block waits (bounded) for its copy before it exits.
+template <int S> __global__ void __launch_bounds__(kThreads) update_rows_staged_kernel(const UpdateArgs p)
+{
+    extern __shared__ __align__(128) unsigned char srow[];
+    __shared__ __align__(8) unsigned long long sbar;
+    const long long r = blockIdx.x;
+    if (r >= p.rows)
+        return;
+    const unsigned int eb = p.src_f64 ? 8u : 4u;
+    const unsigned int nbytes = (unsigned int)p.n * eb;
+    const unsigned int bulk = nbytes & ~15u;
+    const unsigned char *g = static_cast<const unsigned char *>(p.src) + (size_t)r * (size_t)p.lda * eb;
+    const unsigned int bar = smem_u32(&sbar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bulk);
+        bulk_g2s(smem_u32(srow), g, bulk, bar);
+    }
+    for (unsigned int q = bulk + threadIdx.x; q < nbytes; q += kThreads)
+        srow[q] = g[q];
+    __syncthreads();   // the barrier is initialised before any thread polls it
+    const bool ok = mbar_wait_bounded(bar, 0u);
+    if (bar_all_or(kThreads, ok ? 0 : 1)) {
+        if (threadIdx.x == 0) {
+            atomicOr(p.flags, PREPF_TIMEOUT);
+            mbar_wait_bounded(bar, 0u);
+        }
+        return;
+    }
+    update_row<S, int, true>(p, r, srow);
 }
 
 // Binary64-accurate ||a_i||^2 of stored rows, one block per row: the
@@ -318,11 +449,49 @@ cudaError_t stored_norms64_launch(int storage, cudaStream_t s, const void *A, co
     return cudaGetLastError();
 }
 
+template <int S> cudaError_t staged_launch(unsigned grid, size_t smem, cudaStream_t s, const UpdateArgs &a)
+{
+    static size_t set = 0;   // the kernel's dynamic shared-memory limit, raised once per size
+    if (smem > set) {
+        const cudaError_t e = cudaFuncSetAttribute(update_rows_staged_kernel<S>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        set = smem;
+    }
+    update_rows_staged_kernel<S><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The staged kernel takes rows of up to this many source bytes (two blocks
+// per SM), whose start is 16-byte aligned on every row.
+constexpr size_t kStagedMaxBytes = 112 * 1024;
+constexpr size_t kStagedMinBytes = 4096;
+
 cudaError_t update_rows_launch(int storage, cudaStream_t s, const UpdateArgs &a)
 {
     if (a.rows <= 0)
         return cudaSuccess;
     const unsigned grid = (unsigned)a.rows;
+    const size_t eb = a.src_f64 ? 8 : 4;
+    const size_t nbytes = (size_t)a.n * eb;
+    const bool aligned = ((uintptr_t)a.src % 16 == 0) && (((size_t)a.lda * eb) % 16 == 0);
+    const char *env = std::getenv("NSLI_UPDATE_STAGED");
+    // FP8 rows stay on the global-memory kernel: their conversions make the
+    // kernel issue-bound, and the staged kernel's fewer resident warps
+    // (two or three blocks per SM) measured slower there (5.25 against 4.92
+    // ms per rewrite-and-iterate step at 131072 x 16384)
+    const bool staged_ok = !(env && env[0] == '0') && storage != NSLI_FP8E4M3 && aligned &&
+                           nbytes >= kStagedMinBytes && nbytes <= kStagedMaxBytes && a.ld < (1ll << 31);
+    if (staged_ok) {
+        const size_t smem = (nbytes + 127) & ~(size_t)127;
+        switch (storage) {
+        case NSLI_F64: return staged_launch<NSLI_F64>(grid, smem, s, a);
+        case NSLI_F32: return staged_launch<NSLI_F32>(grid, smem, s, a);
+        case NSLI_BF16: return staged_launch<NSLI_BF16>(grid, smem, s, a);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (storage) {
     case NSLI_F64: update_rows_kernel<NSLI_F64><<<grid, kThreads, 0, s>>>(a); break;
     case NSLI_F32: update_rows_kernel<NSLI_F32><<<grid, kThreads, 0, s>>>(a); break;

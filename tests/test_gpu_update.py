@@ -131,3 +131,45 @@ def test_update_rows_on_sparse_handle_unsupported():
         with pytest.raises(nsli.NsliError) as e:
             s.update_rows(0, np.ones((1, 40), np.float32))
         assert e.value.code == nsli.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("n, pad", [(1024, 0), (1027, 1), (20000, 0), (30000, 0)])
+def test_staged_and_global_update_paths_agree(storage, n, pad, monkeypatch):
+    """Rows short enough for shared memory and 16-byte aligned are staged
+    there by one bulk copy (with a ragged tail when n * 4 is not a multiple
+    of 16: n = 1027 from a source of pitch 1028); longer ones (n = 30000
+    from binary32, n >= 20000 from binary64) and FP8 rows read global
+    memory.  Either way the updated rows equal rows created from the same
+    values, bit for bit, and the two paths give the same stored values and
+    norms."""
+    import ctypes
+    import torch
+    m = 48
+    p = workloads.dense_system(m, n, seed=71)
+    q = workloads.dense_system(m, n, seed=72)
+    lib = nsli.load()
+    srcq = src(q["A"], storage)
+    dev = torch.zeros((m, n + pad), dtype=torch.float64 if storage == "f64" else torch.float32,
+                      device="cuda")
+    dev[:, :n] = torch.from_numpy(srcq).cuda()
+    a_dtype = nsli.F64 if storage == "f64" else nsli.F32
+    torch.cuda.synchronize()
+    results = []
+    with nsli.Solver(srcq, q["b0"], p["x0"], Av=p["Av"], storage=storage) as t:
+        want_rows, want_n2 = t.stored_rows(), t.norms2()
+        for staged in ("1", "0"):
+            monkeypatch.setenv("NSLI_UPDATE_STAGED", staged)
+            with nsli.Solver(src(p["A"], storage), q["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
+                rc = lib.nsli_update_rows(s._h, 0, m, a_dtype, ctypes.c_void_p(dev.data_ptr()), n + pad, None)
+                assert rc == nsli.OK
+                rows, n2 = s.stored_rows(), s.norms2()
+                np.testing.assert_array_equal(rows, want_rows)
+                np.testing.assert_array_equal(n2, want_n2)
+                ys, hs, sts = s.map_reduce()
+                yt, ht, stt = t.map_reduce()
+                np.testing.assert_array_equal(ys, yt)
+                assert hs == ht and sts == stt
+                results.append((rows, n2))
+    np.testing.assert_array_equal(results[0][0], results[1][0])
+    np.testing.assert_array_equal(results[0][1], results[1][1])
