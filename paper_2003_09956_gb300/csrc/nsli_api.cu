@@ -1172,6 +1172,21 @@ int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows, int32_t a_dtype,
         if (err == cudaSuccess && (!on_device || b0) && r0 + cnt < rows)
             err = cudaStreamSynchronize(s);  // staging buffers are reused
     }
+    if (err == cudaSuccess) {
+        // the records of the rows (rejected rows: rebuilt from their
+        // unchanged norm, b0 and scale), as at creation
+        MetaArgs ma;
+        ma.meta = h->meta;
+        ma.b0_64 = h->b0_64;
+        ma.av_64 = h->av_64;
+        ma.n2_64 = h->n2_meta;
+        ma.scale = h->scale;
+        ma.m = rows;
+        ma.row0 = row0;
+        ma.flags = h->flags;
+        err = meta_launch(h->storage == NSLI_F64, s, ma);
+        h->launches += 1;
+    }
     if (stage) {
         if (err == cudaSuccess)
             err = cudaStreamSynchronize(s);
@@ -1696,13 +1711,18 @@ int rebuild_tables(nsli_pool p)
         p->live_order.push_back((int)sid);
     }
     // The persistent launch takes the items in table order from a shared
-    // counter: put first the items that stream fewest bytes per unit of
-    // time (problems whose rows occupy fewest of the CTA's threads), so the
-    // long ones start early and the short ones fill the end of the phase.
-    // Which CTA maps an item changes no result.
-    std::stable_sort(items.begin(), items.end(), [&probs](const GroupItem &a, const GroupItem &b) {
-        return probs[a.prob].nt < probs[b.prob].nt;
-    });
+    // counter: longest first (list scheduling by longest processing time),
+    // so the long items start early and the short ones fill the end of the
+    // phase.  An item's time is estimated as its bytes of A over the share
+    // of the CTA's threads its rows occupy.  Which CTA maps an item changes
+    // no result.
+    auto est = [&probs](const GroupItem &it) {
+        const GroupProblem &gp = probs[it.prob];
+        return (double)(it.row_end - it.row_begin) * (double)gp.map.row_bytes * (double)kMapMaxConsumers /
+               (double)std::max(1, gp.nt);
+    };
+    std::stable_sort(items.begin(), items.end(),
+                     [&est](const GroupItem &a, const GroupItem &b) { return est(a) > est(b); });
     int rc;
     if ((rc = grow(p, &p->d_probs, &p->cap_probs, std::max<size_t>(1, probs.size()))) != NSLI_OK)
         return rc;

@@ -259,8 +259,9 @@ struct MetaArgs {
     void *meta;
     const double *b0_64, *av_64, *n2_64;
     const float *scale;
-    long long m;
+    long long m;            // rows [row0, row0 + m)
     int *flags;
+    long long row0 = 0;
 };
 cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a);
 

@@ -1669,8 +1669,9 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
 
     // ||a_i||^2 of the stored values: binary64 for binary64 storage, else the
     // double-float accumulation of nsli_sumsq.cuh, folded into binary64 every
-    // 8 entries (fast = 0: the binary64 norms) or only at the end (fast = 1:
-    // the norm behind the row records, as in the row-update kernel)
+    // 8 entries (fast = 0: the binary64 norms) or not at all (fast = 1: the
+    // norm behind the row records, as in the row-update kernel), and the
+    // block total of sumsq_block_total
     double n2 = 0.0;
     SumSq sq = sumsq_init();
     for (long long j = threadIdx.x; j < p.ld; j += blockDim.x) {
@@ -1692,10 +1693,12 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
             const float a = in ? s32[j] : 0.0f;
             if (in && !isfinite(a))
                 bad = 1;
+            // (a value that rounds to infinity makes the norm infinite and
+            // the row invalid, as in the row-update kernel)
             const __nv_bfloat16 q = __float2bfloat16_rn(a);
             static_cast<__nv_bfloat16 *>(p.A)[gi * p.ld + j] = q;
             const float v = __bfloat162float(q);
-            if (in && isfinite(v))
+            if (in)
                 p.fast ? sumsq_add<0>(sq, v) : sumsq_add<8>(sq, v);
         } else {
             const float a = in ? s32[j] : 0.0f;
@@ -1707,18 +1710,23 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
                 p.fast ? sumsq_add<0>(sq, v) : sumsq_add<8>(sq, v);
         }
     }
-    if (S != NSLI_F64)
-        n2 = sumsq_value(sq);
-    n2 = warp_sum(n2);
     if (bad)
         sbad = 1;
-    if (lane == 0)
-        sred[wid] = n2;
-    __syncthreads();
+    double t = 0.0;   // the row total, in thread 0
+    if constexpr (S != NSLI_F64) {
+        __shared__ float2 spair[8];
+        __shared__ double sacc[8];
+        t = sumsq_block_total<8>(sq, spair, sacc);   // (synchronises the block)
+    } else {
+        n2 = warp_sum(n2);
+        if (lane == 0)
+            sred[wid] = n2;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                t += sred[q];
+    }
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-            t += sred[q];
         if (p.norms_in != nullptr)
             t = p.norms_in[gi];
         p.n2_64[gi] = t;
@@ -1735,9 +1743,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs p)
 template <bool F64>
 __global__ void __launch_bounds__(256) meta_kernel(const MetaArgs p)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.m)
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.m)
         return;
+    const long long i = p.row0 + k;
     const double b0 = p.b0_64[i];
     const double av = p.av_64[i];
     const double n2 = p.n2_64[i];
@@ -2081,6 +2090,8 @@ cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a)
 
 cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a)
 {
+    if (a.m <= 0)
+        return cudaSuccess;
     const unsigned int grid = (unsigned int)((a.m + 255) / 256);
     if (f64)
         meta_kernel<true><<<grid, 256, 0, s>>>(a);

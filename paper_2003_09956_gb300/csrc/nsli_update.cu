@@ -8,7 +8,8 @@
 // arithmetic as the set-up kernel (so a row gets the same norm whether it
 // came with nsli_create or with an update).  A row that is not finite or is
 // all zeros is left as it was and flagged; otherwise pass 2 writes the
-// stored values, its norm, the new b0 if one was given, and the row record.
+// stored values, its norm, the new b0 if one was given and its FP8 scale,
+// and the set-up's record kernel then rebuilds the records of the rows.
 // Where the source row fits in shared memory and is 16-byte aligned, one
 // bulk copy stages it there first, so both passes read it from shared
 // memory (A's source is read from HBM once, and no thread waits on a
@@ -273,36 +274,51 @@ template <int S, typename I, bool VEC> __device__ __forceinline__ void update_ro
                 const I j = j0 + (I)u * kThreads;
                 v[u] = j < n ? stored_value_f<S>(src, f64src, j, inv_scale, scale, &bad) : 0.0f;
             }
+            // (a row with a non-finite value is rejected below, so its sum
+            // may take the value as it is)
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
-                if (isfinite(v[u]))
-                    sumsq_add<0>(sq, v[u]);
+                sumsq_add<0>(sq, v[u]);
         }
     }
-    if (S != NSLI_F64)
-        n2 = sumsq_value(sq);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
     if (bad)
         sbad = 1;
-    if (lane == 0)
-        sred[wid] = n2;
-    __syncthreads();
+    // the row total in thread 0, as the set-up kernel takes it; thread 0
+    // alone decides: a binary64 instruction occupies GB300's binary64 pipe
+    // for a whole warp however few lanes it has, so the other warps skip it
     double t = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q)
-        t += sred[q];
-    const double b_new = p.b0_new ? p.b0_new[r] : 0.0;
-    int f = 0;
-    if (sbad || !isfinite(t) || (p.b0_new && !isfinite(b_new)))
-        f |= PREPF_NONFINITE;
-    else if (t == 0.0)
-        f |= PREPF_ZERO_ROW;
-    if (f) {
+    if constexpr (S != NSLI_F64) {
+        __shared__ float2 spair[kThreads / 32];
+        __shared__ double sacc[kThreads / 32];
+        t = sumsq_block_total<kThreads / 32>(sq, spair, sacc);   // (synchronises the block)
+    } else {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+        if (lane == 0)
+            sred[wid] = n2;
+        __syncthreads();
         if (threadIdx.x == 0)
-            atomicOr(p.flags, f);
-        return;   // the row keeps its previous values
+            for (int q = 0; q < kThreads / 32; ++q)
+                t += sred[q];
     }
+    __shared__ double st;
+    __shared__ int sflag;
+    if (threadIdx.x == 0) {
+        const double b_new = p.b0_new ? p.b0_new[r] : 0.0;
+        int f = 0;
+        if (sbad || !isfinite(t) || (p.b0_new && !isfinite(b_new)))
+            f |= PREPF_NONFINITE;
+        else if (t == 0.0)
+            f |= PREPF_ZERO_ROW;
+        if (f)
+            atomicOr(p.flags, f);
+        st = t;
+        sflag = f;
+    }
+    __syncthreads();
+    if (sflag)
+        return;   // the row keeps its previous values
 
     // pass 2: store (zero padding up to ld), then the row's norm and record
     void *Arow = static_cast<unsigned char *>(p.A) + (size_t)gi * (size_t)p.ld * stored_bytes<S>();
@@ -317,24 +333,14 @@ template <int S, typename I, bool VEC> __device__ __forceinline__ void update_ro
                 store_value<S>(Arow, j, src, f64src, j, j < n, inv_scale);
         }
     }
+    // the row's norm, b0 and FP8 scale; its record is rebuilt from them by
+    // the set-up's record kernel (one thread per row), after this launch
     if (threadIdx.x == 0) {
-        p.n2_64[gi] = t;
+        p.n2_64[gi] = st;
         if (p.b0_new)
-            p.b0_64[gi] = b_new;
-        const double b0 = p.b0_new ? b_new : p.b0_64[gi];
-        const double av = p.av_64[gi];
-        const double inv_n2 = 1.0 / t;
-        const double inv_n = 1.0 / sqrt(t);
-        if (S == NSLI_F64) {
-            RowMeta64 m{b0, av, inv_n2, inv_n};
-            static_cast<RowMeta64 *>(p.meta)[gi] = m;
-        } else {
-            if (S == NSLI_FP8E4M3)
-                p.scale[gi] = scale;
-            RowMeta32 m{(float)b0, (float)av, (float)inv_n2, (float)inv_n,
-                        (S == NSLI_FP8E4M3) ? scale : 1.0f, 0.0f, 0.0f, 0.0f};
-            static_cast<RowMeta32 *>(p.meta)[gi] = m;
-        }
+            p.b0_64[gi] = p.b0_new[r];
+        if (S == NSLI_FP8E4M3)
+            p.scale[gi] = scale;
     }
 }
 

@@ -173,3 +173,51 @@ def test_staged_and_global_update_paths_agree(storage, n, pad, monkeypatch):
                 results.append((rows, n2))
     np.testing.assert_array_equal(results[0][0], results[1][0])
     np.testing.assert_array_equal(results[0][1], results[1][1])
+
+
+def test_bf16_rounding_of_created_and_updated_rows_at_the_edges():
+    """bf16 storage rounds to nearest, ties to even, in the set-up and the
+    row-update kernels alike (the scalar and the paired conversion): ties of
+    both parities,
+    subnormal values and ties, signed zeros and values next to the largest
+    bf16 are stored as the oracle's rounding gives them, whether the row was
+    created or updated; a value that rounds to infinity makes its row
+    invalid in both."""
+    import torch
+    n = 2048
+    rng = np.random.default_rng(81)
+    base = (np.arange(1, 513, dtype=np.uint32) << np.uint32(16)) | np.uint32(0x3f800000)
+    ties = (base + np.uint32(0x8000)).view(np.float32)              # halfway, both parities
+    sub = ((np.arange(1, 257, dtype=np.uint32) << np.uint32(16)) + np.uint32(0x8000)).view(np.float32)
+    near = np.array([3.3895314e38, -3.3895314e38, 3.38e38, 1.17549435e-38, -1.17549435e-38,
+                     1e-40, -1e-40, 0.0, -0.0, 1.0], np.float32)
+    rows = np.zeros((8, n), np.float32)
+    rows[0, :512] = ties
+    rows[1, :512] = -ties
+    rows[2, :256] = sub
+    rows[2, 256] = 1.0
+    rows[3, :256] = -sub
+    rows[3, 256] = -1.0
+    rows[4, :10] = near
+    rows[5:] = rng.standard_normal((3, n)).astype(np.float32)
+    p = workloads.dense_system(8, n, seed=82)
+    want = oracle.quantize_bf16(rows).astype(np.float64)
+    with nsli.Solver(rows, p["b0"], p["x0"], storage="bf16") as t:
+        np.testing.assert_array_equal(t.stored_rows(), want)
+        n2_created = t.norms2()
+    with nsli.Solver(p["A"], p["b0"], p["x0"], storage="bf16") as s:
+        s.update_rows(0, torch.from_numpy(rows).cuda())
+        np.testing.assert_array_equal(s.stored_rows(), want)
+        np.testing.assert_array_equal(s.norms2(), n2_created)
+        before = s.stored_rows()
+        bad = rows[5:6].copy()
+        bad[0, 3] = 3.4e38                                           # rounds to infinity in bf16
+        with pytest.raises(nsli.NsliError) as e:
+            s.update_rows(5, torch.from_numpy(bad).cuda())
+        assert e.value.code == nsli.ERR_NONFINITE
+        np.testing.assert_array_equal(s.stored_rows(), before)
+    with pytest.raises(nsli.NsliError) as e:
+        bad_all = rows.copy()
+        bad_all[6, 3] = 3.4e38
+        nsli.Solver(bad_all, p["b0"], p["x0"], storage="bf16")
+    assert e.value.code == nsli.ERR_NONFINITE
