@@ -101,6 +101,8 @@ def parse_args():
     ap.add_argument("--oracle-model-seeds", type=int, default=10,
                     help="model-system seeds solved by the FP64 oracle beside the GPU's")
     ap.add_argument("--cfg2", type=int, default=1, help="time the 32768 x 8192 system at rho 0, 1e-4, 1e-3")
+    ap.add_argument("--long-rows", default="f32,bf16",
+                    help="storage types timed on the 108001 x 54000 system (the paper's n); '' to skip")
     ap.add_argument("--feasibility", default="dense-8192x2048",
                     help="system solved to binary64-confirmed max r_i <= 1e-6 max|b| per storage ('' for none)")
     ap.add_argument("--feasibility-only", action="store_true", help="run only the solves to feasibility")
@@ -722,6 +724,28 @@ def time_cfg2(nsli, torch, steps, warmup, dist, world, peak):
     return out
 
 
+def time_long_rows(nsli, torch, storages, steps, warmup, dist, world, peak):
+    """The paper's row length n = 54000 (m = 2n + 1 rows, A 21.7 GiB in
+    binary32): rows longer than the register-resident limit, mapped on
+    thread-block clusters, per storage type."""
+    from paper_2003_09956_gb300 import workloads
+
+    w0 = WORKLOADS["dense-108001x54000"]
+    p = workloads.dense_system(w0["m"], w0["n"], seed=w0["seed"])
+    out = {}
+    for st in storages:
+        s, _, r = time_storage(nsli, torch, p, st, w0, steps, warmup, dist, world)
+        s.close()
+        mb = map_bytes(w0["m"], w0["n"], st)
+        out[st] = {"value": world * steps / (r["ms"] / 1000.0), "unit": UNIT, "ms_per_step": r["ms"] / steps,
+                   "map_ms_avg": r["map_ms_avg"], "map_gbs": mb / (r["map_ms_avg"] / 1000.0) / 1e9,
+                   "map_frac_of_measured_hbm": mb / (r["map_ms_avg"] / 1000.0) / 1e9 / peak,
+                   "max_viol_f64": r["max_viol_f64"], "gpu_launches": r["launches"]}
+    del p
+    torch.cuda.empty_cache()
+    return out
+
+
 FEASIBILITY = {
     "dense-8192x2048": {"m": 8192, "n": 2048, "seed": 3001},
     "dense-16384x4096": {"m": 16384, "n": 4096, "seed": 3002},
@@ -968,6 +992,9 @@ def main():
         variants["persistent_pool_bf16"] = time_pool_rounds(nsli, torch, args.pool, args.pool_rounds, 2, peak)
     if args.cfg2:
         variants["dense-32768x8192_f32"] = time_cfg2(nsli, torch, K, W, dist, world, peak)
+    if args.long_rows:
+        variants["dense-108001x54000"] = time_long_rows(nsli, torch, [v for v in args.long_rows.split(",") if v],
+                                                        min(K, 20), W, dist, world, peak)
     if args.feasibility:
         variants["solve_to_feasibility"] = time_feasibility(nsli, args.feasibility)
     finals = [main_run["final"]]
