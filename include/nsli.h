@@ -191,11 +191,14 @@ int nsli_update_b(nsli_handle h, const double *b0, int64_t tick);
  *            the same rows, or NULL to keep them.
  * The rows are stored, normed (binary64, from the stored values) and their
  * records rebuilt exactly as nsli_create does.  A row that holds a NaN / Inf
- * (or whose new b0 does) or is all zeros keeps its previous values; the call
- * then returns NSLI_ERR_NONFINITE or NSLI_ERR_ZERO_ROW after updating the
- * other rows.  Other errors: NSLI_ERR_ARG (range outside [0, m), NULL A,
- * lda < n, dtype), NSLI_ERR_UNSUPPORTED (a sparse handle), NSLI_ERR_OOM /
- * NSLI_ERR_CUDA.  Synchronises (it reads the row flags back). */
+ * (or whose new b0 does, or a value that rounds to infinity in bf16) or is
+ * all zeros keeps its previous values; the call then returns
+ * NSLI_ERR_NONFINITE or NSLI_ERR_ZERO_ROW after updating the other rows.
+ * Other errors: NSLI_ERR_ARG (range outside [0, m), NULL A, lda < n,
+ * dtype), NSLI_ERR_UNSUPPORTED (a sparse handle), NSLI_ERR_TIMEOUT (a
+ * device copy of a source row did not arrive within the bounded wait; that
+ * row keeps its previous values), NSLI_ERR_OOM / NSLI_ERR_CUDA.
+ * Synchronises (it reads the row flags back). */
 int nsli_update_rows(nsli_handle h, int64_t row0, int64_t rows,
                      int32_t a_dtype, const void *A, int64_t lda,
                      const double *b0);

@@ -221,3 +221,42 @@ def test_bf16_rounding_of_created_and_updated_rows_at_the_edges():
         bad_all[6, 3] = 3.4e38
         nsli.Solver(bad_all, p["b0"], p["x0"], storage="bf16")
     assert e.value.code == nsli.ERR_NONFINITE
+
+
+def test_fp8_rounding_of_created_and_updated_rows_at_the_edges():
+    """FP8 E4M3 storage (per-row power-of-two scales) rounds to nearest, ties
+    to even, in the set-up and the row-update kernels alike: every value
+    halfway between two neighbouring codes, normal and subnormal, both
+    signs, the codes themselves and signed zeros are stored as the oracle's
+    rounding gives them."""
+    import torch
+    n = 1024
+    codes = np.arange(0, 0x7E, dtype=np.uint32)
+
+    def decode(c):
+        e = (c >> 3) & 0xF
+        m = c & 7
+        return np.where(e == 0, m * 2.0 ** -9, (1 + m / 8.0) * 2.0 ** (e.astype(np.int64) - 7))
+
+    v0, v1 = decode(codes), decode(codes + 1)
+    ties = ((v0 + v1) / 2).astype(np.float32)
+    rows = np.zeros((6, n), np.float32)
+    for r, vals in enumerate([ties, -ties, v0.astype(np.float32), -v0.astype(np.float32)]):
+        rows[r, :vals.size] = vals
+        rows[r, n - 1] = 448.0          # row scale 1: the values are the codes' own
+    rows[4, :4] = [0.0, -0.0, 448.0, -2.0 ** -9]
+    rows[4, 4:] = np.random.default_rng(83).standard_normal(n - 4).astype(np.float32) * 1e-3
+    rows[5] = np.random.default_rng(84).standard_normal(n).astype(np.float32) * 37.0
+    want, _ = oracle.quantize_e4m3_rows(rows)
+    p = workloads.dense_system(6, n, seed=85)
+    with nsli.Solver(rows, p["b0"], p["x0"], storage="fp8") as t:
+        np.testing.assert_array_equal(t.stored_rows(), want.astype(np.float64))
+        n2_created = t.norms2()
+        yt, ht, stt = t.map_reduce()
+    with nsli.Solver(p["A"], p["b0"], p["x0"], storage="fp8") as s:
+        s.update_rows(0, torch.from_numpy(rows).cuda())
+        np.testing.assert_array_equal(s.stored_rows(), want.astype(np.float64))
+        np.testing.assert_array_equal(s.norms2(), n2_created)
+        ys, hs, sts = s.map_reduce()
+    np.testing.assert_array_equal(ys, yt)
+    assert hs == ht and sts == stt
