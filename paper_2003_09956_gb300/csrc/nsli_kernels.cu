@@ -1197,15 +1197,21 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
     }
     __syncthreads();
     if (step && grp == 0) {
-        double y = 0.0;
-        if constexpr (sizeof(Acc) == 8 && NGRP == 8) {
-            y = ((sh.part[0][lane] + sh.part[1][lane]) + (sh.part[2][lane] + sh.part[3][lane])) +
-                ((sh.part[4][lane] + sh.part[5][lane]) + (sh.part[6][lane] + sh.part[7][lane]));
-        } else {
+        // the NGRP group sums added pairwise (adjacent pairs, log2 NGRP
+        // levels): a chain of dependent binary64 adds costs ~435 cycles a
+        // link on this part
+        static_assert((NGRP & (NGRP - 1)) == 0, "a power-of-two number of groups");
+        double v[NGRP];
 #pragma unroll
-            for (int q = 0; q < NGRP; ++q)
-                y += sh.part[q][lane];
+        for (int q = 0; q < NGRP; ++q)
+            v[q] = sh.part[q][lane];
+#pragma unroll
+        for (int w = NGRP / 2; w >= 1; w /= 2) {
+#pragma unroll
+            for (int q = 0; q < w; ++q)
+                v[q] = v[2 * q] + v[2 * q + 1];
         }
+        const double y = v[0];
         double val = 0.0;
         if (j < p.ld) {
             if (rule == NSLI_RULE_MODAP) {
@@ -1239,10 +1245,16 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
     double dx2 = 0.0, ynorm = 0.0;
     if (step) {
         if (grp == 0) {
-            double v = 0.0;
-#pragma unroll 4
-            for (int q = lane; q < nblk; q += 32)
-                v += __ldcg(p.part_dx + q);
+            // four running sums per lane (blocks q = lane + 32 (4c + u)),
+            // added pairwise: a quarter of the dependent binary64 adds
+            double v4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int q = lane; q < nblk; q += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q + 32 * u < nblk)
+                        v4[u] += __ldcg(p.part_dx + q + 32 * u);
+            }
+            double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
             v = warp_sum(v);
             if (lane == 0)
                 sh.red[0] = v;
