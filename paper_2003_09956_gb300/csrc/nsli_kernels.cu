@@ -1108,12 +1108,23 @@ __device__ __forceinline__ double red_ord_dec(unsigned long long u)
     return __longlong_as_double((long long)bits);
 }
 
-template <typename SH> __device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, SH &sh)
+// Barrier of the threads that run one reduce item: the whole block
+// (bar_id < 0) or the named barrier bar_id of nthr threads.
+__device__ __forceinline__ void sub_sync(int bar_id, int nthr)
 {
-    const int lane = threadIdx.x & 31;
+    if (bar_id < 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+}
+
+template <typename SH>
+__device__ __forceinline__ void reduce_stats(const PartStat *ps, int G, SH &sh, int tid = threadIdx.x)
+{
+    const int lane = tid & 31;
     // maxima as order-preserving integers: exact, and no binary64 compare
     // (a long dependency chain on GB300) on the way
-    if (threadIdx.x < 32) {
+    if (tid < 32) {
         long long h = 0;
         unsigned long long mv = red_ord_enc(-INFINITY), mn = mv, mb = red_ord_enc(0.0);
 #pragma unroll 4
@@ -1145,14 +1156,18 @@ template <typename SH> __device__ __forceinline__ void reduce_stats(const PartSt
 // reduce kernels, 16 in the persistent serving kernel).
 template <typename Acc, int NGRP = 8>
 __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, const int nblk,
-                                            ReduceSharedT<NGRP> &sh)
+                                            ReduceSharedT<NGRP> &sh, const int tid, const int bar_id)
 {
+    // tid / bar_id: the thread's index within the NGRP warps that run this
+    // item and their barrier (-1: the whole block; else the named barrier
+    // bar_id of NGRP * 32 threads)
+    const int nthr = NGRP * 32;
     DevState *st = p.st;
     if (*(volatile int *)&st->done)
         return;
-    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    reduce_stats(p.part_stat, p.G, sh);
-    __syncthreads();
+    const int lane = tid & 31, grp = tid >> 5;
+    reduce_stats(p.part_stat, p.G, sh, tid);
+    sub_sync(bar_id, nthr);
     const long long h = sh.h;
     const double mv = sh.mv, mn = sh.mn, mb = sh.mb;
     const int stop = st->stop;
@@ -1195,7 +1210,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
         }
         sh.part[grp][lane] = yj;
     }
-    __syncthreads();
+    sub_sync(bar_id, nthr);
     if (step && grp == 0) {
         // the NGRP group sums added pairwise (adjacent pairs, log2 NGRP
         // levels): a chain of dependent binary64 adds costs ~435 cycles a
@@ -1232,12 +1247,12 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             p.part_dx[blk] = val;
     }
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    sub_sync(bar_id, nthr);
+    if (tid == 0) {
         const unsigned int t = atomicAdd(&st->ticket, 1u);
         sh.last = (t == (unsigned int)nblk - 1) ? 1 : 0;
     }
-    __syncthreads();
+    sub_sync(bar_id, nthr);
     if (!sh.last)
         return;
     __threadfence();
@@ -1259,14 +1274,14 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             if (lane == 0)
                 sh.red[0] = v;
         }
-        __syncthreads();
+        sub_sync(bar_id, nthr);
         const double tot = sh.red[0];
         if (rule == NSLI_RULE_MODAP) {
             ynorm = sqrt(tot);
             const double s = ynorm > 0.0 ? lambda / ynorm : 0.0;
             Acc *x = static_cast<Acc *>(p.x);
             double v = 0.0;
-            for (long long q = threadIdx.x; q < p.ld; q += blockDim.x) {
+            for (long long q = tid; q < p.ld; q += nthr) {
                 const double xo = p.x64[q];
                 const double xn = xo - s * __ldcg(p.ybuf + q);
                 p.x64[q] = xn;
@@ -1275,10 +1290,10 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
                 v += d * d;
             }
             v = warp_sum(v);
-            __syncthreads();
+            sub_sync(bar_id, nthr);
             if (lane == 0)
                 sh.red[grp] = v;
-            __syncthreads();
+            sub_sync(bar_id, nthr);
             double t = 0.0;
             for (int q = 0; q < NGRP; ++q)
                 t += sh.red[q];
@@ -1287,7 +1302,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &p, const int blk, 
             dx2 = tot;
         }
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         st->h = h;
         st->maxviol = mv;
         st->maxnorm = mn;
@@ -1318,7 +1333,7 @@ template <typename Acc>
 __global__ void __launch_bounds__(256) reduce_update_kernel(const ReduceArgs p)
 {
     __shared__ ReduceShared sh;
-    reduce_body<Acc>(p, blockIdx.x, gridDim.x, sh);
+    reduce_body<Acc>(p, blockIdx.x, gridDim.x, sh, threadIdx.x, -1);
 }
 
 // Many problems in one launch: block b serves (problem, column block) tab[b].
@@ -1328,7 +1343,7 @@ __global__ void __launch_bounds__(256) reduce_group_kernel(const GroupProblem *p
     __shared__ ReduceShared sh;
     const GroupRed t = tab[blockIdx.x];
     const GroupProblem &gp = probs[t.prob];
-    reduce_body<Acc>(gp.red, t.blk, gp.red_blocks, sh);
+    reduce_body<Acc>(gp.red, t.blk, gp.red_blocks, sh, threadIdx.x, -1);
 }
 
 // Map + Reduce without a step (diagnostics and parity): y in binary64.
@@ -1396,6 +1411,8 @@ __device__ __forceinline__ unsigned long long global_ns()
 // end at byte 1280), and the reduce's shared block in the ring's stages
 // (idle during the Reduce phase), so it needs no shared memory beyond the
 // largest ring of its problems.
+constexpr int kServeRedGrp = 2;   // warps per serving reduce item
+constexpr int kServeRedSub = 8;   // reduce items in flight per CTA
 struct ServeShared {
     unsigned long long t_start;
     int ok, running;
@@ -1505,9 +1522,17 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeA
 {
     using Acc = typename Traits<S>::acc;
     static_assert(sizeof(Acc) == 4, "the serving kernel keeps its words in a binary32 ring header");
-    constexpr int NGRP = kMapMaxConsumers / 32;
+    // Reduce items run kServeRedSub at a time per CTA, each on its own
+    // kServeRedGrp warps (their own named barrier and shared block, placed
+    // in the ring's stages, free in that phase): an item is a chain of
+    // dependent global-memory round trips, and several in flight overlap
+    constexpr int NGRP = kServeRedGrp;
+    constexpr int NSUB = kMapMaxConsumers / (32 * NGRP);
+    static_assert(NSUB == kServeRedSub, "reduce sub-blocks tile the CTA");
     extern __shared__ __align__(128) unsigned char smem[];
-    ReduceSharedT<NGRP> &rsh = *reinterpret_cast<ReduceSharedT<NGRP> *>(smem + kSmemHeader);
+    const int sub = threadIdx.x / (32 * NGRP), stid = threadIdx.x % (32 * NGRP);
+    ReduceSharedT<NGRP> &rsh = reinterpret_cast<ReduceSharedT<NGRP> *>(smem + kSmemHeader)[sub];
+    int *sub_item = reinterpret_cast<int *>(smem + kSmemHeader + NSUB * sizeof(ReduceSharedT<NGRP>));
     ServeShared &ss = serve_shared();
     if (threadIdx.x == 0)
         ss.t_start = global_ns();
@@ -1552,17 +1577,18 @@ __global__ void __launch_bounds__(kMapMaxConsumers, 1) serve_kernel(const ServeA
         if (!serve_grid_sync(a.sync, G))
             break;
         for (;;) {
-            if (threadIdx.x == 0)
-                ss.item = (int)atomicAdd(&a.sync->red_next, 1u);
-            __syncthreads();
-            const int i = ss.item;
+            if (stid == 0)
+                sub_item[sub] = (int)atomicAdd(&a.sync->red_next, 1u);
+            sub_sync(1 + sub, 32 * NGRP);
+            const int i = sub_item[sub];
             if (i >= a.nreds)
                 break;
             const GroupRed t = a.reds[i];
             const GroupProblem &gp = a.probs[t.prob];
-            reduce_body<Acc, NGRP>(gp.red, t.blk, gp.red_blocks, rsh);
-            __syncthreads();
+            reduce_body<Acc, NGRP>(gp.red, t.blk, gp.red_blocks, rsh, stid, 1 + sub);
+            sub_sync(1 + sub, 32 * NGRP);   // the item's shared words are free again
         }
+        __syncthreads();
         if (!serve_grid_sync(a.sync, G))
             break;
     }
