@@ -1094,7 +1094,7 @@ int nsli_update_b(nsli_handle h, const double *b0, int64_t tick)
         ma.scale = h->scale;
         ma.m = h->m;
         ma.flags = h->flags;
-        CK(meta_launch(h->storage == NSLI_F64, h->stream, ma), "update row records");
+        CK(meta_b0_launch(h->storage == NSLI_F64, h->stream, ma), "update row records");
         h->launches += 1;
     }
     if (tick >= 0) {

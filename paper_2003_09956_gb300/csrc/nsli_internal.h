@@ -264,6 +264,8 @@ struct MetaArgs {
     long long row0 = 0;
 };
 cudaError_t meta_launch(bool f64, cudaStream_t s, const MetaArgs &a);
+// only the records' b0 (a new right-hand side)
+cudaError_t meta_b0_launch(bool f64, cudaStream_t s, const MetaArgs &a);
 
 // x64[j] = src[j] (j < n), 0 up to ld; x = x64 rounded to the accumulation type
 cudaError_t x_from_f64_launch(bool f64, cudaStream_t s, const double *src, double *x64, void *x,

@@ -1802,6 +1802,24 @@ __global__ void __launch_bounds__(256) meta_kernel(const MetaArgs p)
     }
 }
 
+// Only the b0 field of rows [row0, row0 + m): a new right-hand side leaves
+// the norms, Av and the FP8 scale as they are, and the field gets the value
+// meta_kernel would give it (no binary64 divide or root per row).
+template <bool F64> __global__ void __launch_bounds__(256) meta_b0_kernel(const MetaArgs p)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.m)
+        return;
+    const long long i = p.row0 + k;
+    const double b0 = p.b0_64[i];
+    if (!isfinite(b0))
+        atomicOr(p.flags, PREPF_NONFINITE);
+    if (F64)
+        static_cast<RowMeta64 *>(p.meta)[i].b0 = b0;
+    else
+        static_cast<RowMeta32 *>(p.meta)[i].b0 = (float)b0;
+}
+
 template <typename Acc>
 __global__ void x_from_f64_kernel(const double *src, double *x64, Acc *x, long long n, long long ld, int *flags)
 {
@@ -2123,6 +2141,18 @@ cudaError_t prep_launch(int storage, cudaStream_t s, const PrepArgs &a)
     case NSLI_FP8E4M3: prep_kernel<NSLI_FP8E4M3><<<grid, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t meta_b0_launch(bool f64, cudaStream_t s, const MetaArgs &a)
+{
+    if (a.m <= 0)
+        return cudaSuccess;
+    const unsigned int grid = (unsigned int)((a.m + 255) / 256);
+    if (f64)
+        meta_b0_kernel<true><<<grid, 256, 0, s>>>(a);
+    else
+        meta_b0_kernel<false><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
