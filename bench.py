@@ -172,6 +172,10 @@ def profiled_traffic(workload, storage):
     return None
 
 
+# GB300's nominal HBM3e bandwidth (context beside the measured copy peak)
+NOMINAL_HBM_GBS = 7900.0
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -1032,6 +1036,7 @@ def main():
                    "graph_block_iters": min(K, 50)},
         "roofline": {"bound": "hbm", "kernel": "map_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "algorithmic_bytes_per_launch": mb,
                      "map_ms_avg": main_run["map_ms_avg"], "reduce_ms_avg": main_run["reduce_ms_avg"],
                      "kernel_pass_ms_per_step": main_run["kernel_pass_ms_per_step"],
