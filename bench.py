@@ -101,6 +101,8 @@ def parse_args():
     ap.add_argument("--oracle-model-seeds", type=int, default=10,
                     help="model-system seeds solved by the FP64 oracle beside the GPU's")
     ap.add_argument("--cfg2", type=int, default=1, help="time the 32768 x 8192 system at rho 0, 1e-4, 1e-3")
+    ap.add_argument("--shards", type=int, default=1,
+                    help="time the benchmark system as two row shards on this GPU (the sharded form's own cost)")
     ap.add_argument("--long-rows", default="f32,bf16",
                     help="storage types timed on the 108001 x 54000 system (the paper's n); '' to skip")
     ap.add_argument("--feasibility", default="dense-8192x2048",
@@ -750,6 +752,60 @@ def time_long_rows(nsli, torch, storages, steps, warmup, dist, world, peak):
     return out
 
 
+def time_shards_one_gpu(nsli, torch, p, storage, w, steps, warmup, fused_ms):
+    """The row-sharded form (ModAPL's sublists, one handle per worker) with
+    R = 2 workers on this one GPU and one stream: each iteration is every
+    worker's Map + local Reduce into its row of the records array (what an
+    allgather delivers on several GPUs) and every worker's global Reduce and
+    step.  The workers run one after the other, so the time against the one
+    handle over all rows is the cost the sharded form adds on the device
+    (its extra launches, the records and the record-based step), without any
+    transport."""
+    from paper_2003_09956_gb300 import shard
+
+    R = 2
+    m, n = p["A"].shape
+    stream = torch.cuda.Stream()
+    ws = []
+    for q in range(R):
+        r0, r1 = shard.row_range(m, R, q)
+        ws.append(nsli.Solver(np.ascontiguousarray(p["A"][r0:r1]), p["b0"][r0:r1], p["x0"], Av=p["Av"][r0:r1],
+                              storage=storage, stream=stream.cuda_stream))
+    recs = torch.zeros((R, shard.HEADER + n), dtype=torch.float64, device="cuda")
+    for s in ws:
+        s.shard_begin(lam=1.0, rule="relaxed", stop="none", max_iter=1 << 40, rho=w["rho"])
+
+    def one():
+        for q, s in enumerate(ws):
+            s.shard_map(recs[q])
+        for s in ws:
+            s.shard_step(recs)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = sum(s.launch_count() for s in ws)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = sum(s.launch_count() for s in ws) - l0
+    xs = [s.get_x() for s in ws]
+    same = all(np.array_equal(xs[0], x) for x in xs[1:])
+    for s in ws:
+        s.close()
+    del recs
+    torch.cuda.empty_cache()
+    return {"workload": "%dx%d %s storage as %d row shards, one handle each, on one GPU" % (m, n, storage, R),
+            "value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms, "fused_ms_per_step": fused_ms,
+            "added_ms_per_step": ms - fused_ms, "record_bytes_per_worker": (shard.HEADER + n) * 8,
+            "workers_hold_the_same_iterate": same, "gpu_launches": launches}
+
+
 FEASIBILITY = {
     "dense-8192x2048": {"m": 8192, "n": 2048, "seed": 3001},
     "dense-16384x4096": {"m": 16384, "n": 4096, "seed": 3002},
@@ -996,6 +1052,9 @@ def main():
         variants["persistent_pool_bf16"] = time_pool_rounds(nsli, torch, args.pool, args.pool_rounds, 2, peak)
     if args.cfg2:
         variants["dense-32768x8192_f32"] = time_cfg2(nsli, torch, K, W, dist, world, peak)
+    if args.shards and world == 1:
+        variants["row_shards_2_on_one_gpu"] = time_shards_one_gpu(nsli, torch, p, args.storage, w, min(K, 20), W,
+                                                                   main_run["ms"] / K)
     if args.long_rows:
         variants["dense-108001x54000"] = time_long_rows(nsli, torch, [v for v in args.long_rows.split(",") if v],
                                                         min(K, 20), W, dist, world, peak)
