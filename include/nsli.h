@@ -77,7 +77,7 @@ enum {
     NSLI_ERR_OOM = -4,         /* device allocation failed                   */
     NSLI_ERR_CUDA = -5,        /* a CUDA runtime call failed (see nsli_last_error) */
     NSLI_ERR_TIMEOUT = -6,     /* a bounded device wait expired              */
-    NSLI_ERR_UNSUPPORTED = -7  /* valid but outside this build's limits      */
+    NSLI_ERR_UNSUPPORTED = -7  /* valid but outside this library's limits    */
 };
 
 typedef struct {
@@ -380,7 +380,7 @@ const char *nsli_batch_last_error(nsli_batch h);
  * iterates are bit-identical alone and in any mix.  Finished problems stop
  * costing work at once (their blocks return) and keep their x until
  * removed.  The paper's master-slave farm (Section 3) runs one problem; the
- * pool is this build's serving form of the same iteration. */
+ * pool is this library's serving form of the same iteration. */
 typedef struct nsli_pool_s *nsli_pool;
 
 /* storage: NSLI_BF16 or NSLI_F32.  max_bytes: device-memory budget of the

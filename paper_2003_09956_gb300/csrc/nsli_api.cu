@@ -535,7 +535,7 @@ const char *nsli_strerror(int code)
     case NSLI_ERR_OOM: return "device memory allocation failed";
     case NSLI_ERR_CUDA: return "CUDA runtime error";
     case NSLI_ERR_TIMEOUT: return "bounded device wait expired";
-    case NSLI_ERR_UNSUPPORTED: return "outside the limits of this build";
+    case NSLI_ERR_UNSUPPORTED: return "outside the limits of this library";
     default: return "unknown status";
     }
 }
