@@ -484,9 +484,9 @@ cudaError_t update_rows_launch(int storage, cudaStream_t s, const UpdateArgs &a)
     const bool aligned = ((uintptr_t)a.src % 16 == 0) && (((size_t)a.lda * eb) % 16 == 0);
     const char *env = std::getenv("NSLI_UPDATE_STAGED");
     // FP8 rows stay on the global-memory kernel: their conversions make the
-    // kernel issue-bound, and the staged kernel's fewer resident warps
-    // (two or three blocks per SM) measured slower there (5.25 against 4.92
-    // ms per rewrite-and-iterate step at 131072 x 16384)
+    // kernel issue-bound, and the staged kernel (two or three resident
+    // blocks per SM) did not measure faster there (4.68 ms per
+    // rewrite-and-iterate step at 131072 x 16384 either way)
     const bool staged_ok = !(env && env[0] == '0') && storage != NSLI_FP8E4M3 && aligned &&
                            nbytes >= kStagedMinBytes && nbytes <= kStagedMaxBytes && a.ld < (1ll << 31);
     if (staged_ok) {
