@@ -286,7 +286,7 @@ int choose_config(nsli_solver *h)
             slot_target = kb * 1024;
     }
     h->guard = (long long)h->consumers * h->vpt != h->nv;
-    const int rg = map_rows_per_group(h->vpt);
+    const int rg = map_rows_per_group(h->vpt, h->storage == NSLI_F64 ? 8 : 4);
     h->R = rg * std::max(1, std::min(64 / rg, slot_target / (h->row_bytes * rg)));
     h->stage_stride = (int)round_up((long long)h->R * h->row_bytes + (long long)h->R * 32, 128);
     const int budget = 232448 - kSmemHeader;

@@ -185,13 +185,19 @@ struct VerifyArgs {
 
 // ---- launchers (nsli_kernels.cu) -------------------------------------------
 constexpr int kMapMaxConsumers = 512;
-constexpr int kMapRowGroup = 4;      // rows reduced per block barrier
+constexpr int kMapRowGroup = 8;      // most rows reduced per block barrier
 constexpr int kReduceCols = 32;      // columns per reduce block
-constexpr int kSmemHeader = 2304;    // barriers, flags, warp-sum buffers
+constexpr int kSmemHeader = 2432;    // barriers, flags, warp-sum buffers
 
 // rows per block barrier of the Map kernel for a vectors-per-thread count;
 // a ring slot always holds a multiple of it
-__host__ __device__ constexpr int map_rows_per_group(int vpt) { return vpt >= 8 ? 1 : (vpt >= 4 ? 2 : 4); }
+// (eight for one vector per thread with binary32 accumulation: short rows,
+// whose fixed cost per barrier would otherwise dominate; the two halves of
+// the warp-sum buffer hold 1024 bytes each)
+__host__ __device__ constexpr int map_rows_per_group(int vpt, int acc_bytes)
+{
+    return vpt >= 8 ? 1 : (vpt >= 4 ? 2 : (vpt >= 2 || acc_bytes > 4 ? 4 : 8));
+}
 
 int map_vpt_limit(int storage);      // largest vectors-per-thread instance
 // guard: some thread's vectors fall outside the row (nv < threads * vpt)

@@ -170,8 +170,30 @@ template <int RG, typename T> __device__ __forceinline__ T warp_fold_rows(const 
         for (int off = 8; off > 0; off >>= 1)
             keep += __shfl_xor_sync(0xffffffffu, keep, off);
         return keep;
+    } else if constexpr (RG == 8) {
+        // lanes [4q, 4q + 4) end with row q: three exchange levels, then a
+        // butterfly over four lanes (the pairing of every level as in the
+        // one-row butterfly)
+        const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+        T k[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const T keep = b4 ? v[q + 4] : v[q];
+            const T send = b4 ? v[q] : v[q + 4];
+            k[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        T m0 = b3 ? k[2] : k[0], m1 = b3 ? k[3] : k[1];
+        const T t0 = b3 ? k[0] : k[2], t1 = b3 ? k[1] : k[3];
+        m0 += __shfl_xor_sync(0xffffffffu, t0, 8);
+        m1 += __shfl_xor_sync(0xffffffffu, t1, 8);
+        T keep = b2 ? m1 : m0;
+        const T send = b2 ? m0 : m1;
+        keep += __shfl_xor_sync(0xffffffffu, send, 4);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+        return keep;
     } else {
-        static_assert(RG == 4, "row groups of 1, 2 or 4");
+        static_assert(RG == 4, "row groups of 1, 2, 4 or 8");
         const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
         T k0 = b4 ? v[2] : v[0], k1 = b4 ? v[3] : v[1];
         const T s0 = b4 ? v[0] : v[2], s1 = b4 ? v[1] : v[3];
@@ -202,7 +224,8 @@ __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_b
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
     constexpr int EPV = Tr::EPV;
-    constexpr int RG = map_rows_per_group(VPT);
+    constexpr int RG = map_rows_per_group(VPT, (int)sizeof(Acc));
+    static_assert(RG * 32 * sizeof(Acc) <= 1024, "a group's warp sums fit half the buffer");
     constexpr int W = 32 / RG;                 // lanes per row in the folded reductions
     constexpr int NCH = (VPT >= 4 && RG <= 2) ? 2 : 1;  // independent chains per row
 
@@ -210,7 +233,7 @@ __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_b
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);  // full[8], empty[8]
-    Acc *red = reinterpret_cast<Acc *>(smem + 256);                          // [2][4][32]
+    Acc *red = reinterpret_cast<Acc *>(smem + 256);                          // two halves of 1024 bytes
     unsigned char *stages = smem + kSmemHeader;
 
     const int tid = threadIdx.x;
@@ -325,7 +348,7 @@ __device__ __forceinline__ void map_body(const MapArgs &p, const long long row_b
                     t += pe[q] + po[q];
                 acc[rr] = t;
             }
-            Acc *rb = red + (grp_counter & 1) * kMapRowGroup * 32;
+            Acc *rb = red + (grp_counter & 1) * (1024 / (int)sizeof(Acc));
             const Acc wsum = warp_fold_rows<RG>(acc, lane);
             if ((lane & (W - 1)) == 0)
                 rb[(lane / W) * 32 + warp] = wsum;
@@ -1418,9 +1441,9 @@ struct ServeShared {
     int ok, running;
     int item;    // the work item the CTA took
 };
-constexpr int kServeSharedOffset = 2048;
+constexpr int kServeSharedOffset = 2304;
 static_assert(kServeSharedOffset + sizeof(ServeShared) <= kSmemHeader, "serving words fit the ring header");
-static_assert(256 + 2 * kMapRowGroup * 32 * sizeof(float) <= kServeSharedOffset, "ring header layout");
+static_assert(256 + 2 * 1024 <= kServeSharedOffset, "ring header layout: barriers, warp sums, serving words");
 __device__ __forceinline__ ServeShared &serve_shared()
 {
     extern __shared__ __align__(128) unsigned char smem[];
