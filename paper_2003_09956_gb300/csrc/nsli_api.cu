@@ -202,19 +202,26 @@ int choose_config(nsli_solver *h)
                     C = c;
             const int slice = C ? (int)((h->nv + C - 1) / C) : 0;
             const int stride = C ? (int)round_up((long long)slice * 16 + 32, 128) : 1;
-            const int ns = C ? std::min(8, (232448 - kSmemHeader) / stride) : 0;
+            const int ns = C ? std::min(16, (232448 - kSmemHeader) / stride) : 0;
             if (C && ns >= 3) {
                 int cv = 1;
                 while ((long long)cv * kMapMaxConsumers < slice)
                     cv *= 2;
-                // rows per block barrier: two for bf16 / FP8 (short row
-                // slices, whose per-row fixed cost dominates) where the
-                // ring holds the groups in use and one more
-                // (NSLI_LONG_CLUSTER_RG forces 1 or 2)
-                int rg = ((h->storage == NSLI_BF16 || h->storage == NSLI_FP8E4M3) && ns >= 6) ? 2 : 1;
+                // rows per block barrier: up to four for FP8 and two for
+                // bf16 (short row slices, whose per-row fixed cost
+                // dominates) where the ring holds the two groups in use and
+                // one more, 3 x rg stages (NSLI_LONG_CLUSTER_RG forces 1, 2
+                // or 4 within those limits)
+                const int rg_max = h->storage == NSLI_FP8E4M3 ? 4 : (h->storage == NSLI_BF16 ? 2 : 1);
+                int rg = 1;
+                for (int v = rg_max; v >= 2; v /= 2)
+                    if (ns >= 3 * v) {
+                        rg = v;
+                        break;
+                    }
                 if (const char *rs = std::getenv("NSLI_LONG_CLUSTER_RG")) {
                     const int v = std::atoi(rs);
-                    if (v == 1 || (v == 2 && ns >= 6 && h->storage != NSLI_F64 && h->storage != NSLI_F32))
+                    if ((v == 1 || v == 2 || v == 4) && v <= rg_max && ns >= 3 * v)
                         rg = v;
                 }
                 int clusters = 0;

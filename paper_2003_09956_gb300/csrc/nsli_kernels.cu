@@ -765,14 +765,15 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(unsigned int bar, unsi
 }
 
 // shared-memory header of the cluster Map (within kSmemHeader)
-constexpr int kClXB = 8;        // exchange buffers (group k uses k % 8)
-constexpr int kClFull = 0;      // 8 full barriers (stages)
-constexpr int kClXbar = 64;     // 8 exchange barriers
-constexpr int kClEmpty = 128;   // 8 empty barriers (stages)
-constexpr int kClRed = 512;     // [2][2][16] warp sums
-constexpr int kClXch = 1024;    // [8][2][8] exchanged partial dots
-static_assert(kClRed + 2 * 2 * 16 * 8 <= kClXch, "cluster Map warp sums fit");
-static_assert(kClXch + kClXB * 2 * 8 * 8 <= kSmemHeader, "cluster Map header fits");
+constexpr int kClXB = 8;          // exchange buffers (group k uses k % 8)
+constexpr int kClMaxStages = 16;  // ring stages (one row slice each)
+constexpr int kClFull = 0;        // 16 full barriers (stages)
+constexpr int kClXbar = 128;      // 8 exchange barriers
+constexpr int kClEmpty = 192;     // 16 empty barriers (stages)
+constexpr int kClRed = 512;       // [2][RG][16] warp sums (at most 512 bytes)
+constexpr int kClXch = 1024;      // [8][RG][8] exchanged partial dots (at most 1024 bytes)
+static_assert(kClEmpty + kClMaxStages * 8 <= kClRed, "cluster Map barriers fit");
+static_assert(kClXch + 1024 <= kSmemHeader, "cluster Map header fits");
 
 // 512 threads map; a 17th warp (the exchange warp) issues the bulk copies,
 // waits for the exchanges, adds the warps' sums and sends the partial dots,
@@ -781,15 +782,17 @@ static_assert(kClXch + kClXB * 2 * 8 * 8 <= kSmemHeader, "cluster Map header fit
 constexpr int kClusterCompute = 512;
 constexpr int kClusterThreads = kClusterCompute + 32;
 
-// RG = rows per group (1 or 2): the rows of a group share one block barrier
-// and one exchange message, and their dependent chains interleave.  The
+// RG = rows per group (1, 2 or 4): the rows of a group share one block
+// barrier and one exchange message, and their dependent chains interleave.  The
 // arithmetic of every row is the same for both (the warp fold of two rows
 // adds the same operands in the same tree as one warp butterfly per row,
 // and rows enter y in row order).
 template <int S, int VPT, int RG>
 __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const MapArgs p)
 {
-    static_assert(RG == 1 || RG == 2, "one or two rows per group");
+    static_assert(RG == 1 || RG == 2 || RG == 4, "one, two or four rows per group");
+    static_assert(2 * RG * 16 * sizeof(typename Traits<S>::acc) <= kClXch - kClRed, "warp sums fit");
+    static_assert(kClXB * RG * 8 * sizeof(typename Traits<S>::acc) <= 1024, "exchange buffers fit");
     using Tr = Traits<S>;
     using Acc = typename Tr::acc;
     using Meta = typename Tr::meta;
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
             }
             const Acc ws = warp_fold_rows<RG>(acc, lane);   // lanes [16q, 16q + 16) end with row q
             if ((lane & (32 / RG - 1)) == 0)
-                red[(g & 1) * 32 + (lane / (32 / RG)) * 16 + warp] = ws;
+                red[(g & 1) * (RG * 16) + (lane / (32 / RG)) * 16 + warp] = ws;
         }
         if (leader && g >= D) {
             const int t = g - D;
@@ -920,22 +923,28 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
             break;
         if (xw) {
             if (g < ngroups) {
-                // the mapping warps' sums in a fixed butterfly (row q in
-                // lanes [16q, 16q + 16)); lane q sends this CTA's partial
-                // dots of the group to CTA q
-                Acc tot = (RG == 2 || lane < NCW) ? red[(g & 1) * 32 + lane] : Acc(0);
+                // the mapping warps' sums in a fixed butterfly, 32 at a time
+                // (rows 2h and 2h + 1 in lanes [0, 16) and [16, 32) of
+                // chunk h); lane q sends this CTA's partial dots of the
+                // group to CTA q
+                constexpr int NCHK = RG >= 2 ? RG / 2 : 1;
+                Acc rowv[RG];
 #pragma unroll
-                for (int off = 8; off > 0; off >>= 1)
-                    tot += __shfl_xor_sync(0xffffffffu, tot, off);
-                Acc t1 = Acc(0);
-                if constexpr (RG == 2)
-                    t1 = __shfl_sync(0xffffffffu, tot, 16);
+                for (int h = 0; h < NCHK; ++h) {
+                    Acc tot = (RG >= 2 || lane < NCW) ? red[(g & 1) * (RG * 16) + h * 32 + lane] : Acc(0);
+#pragma unroll
+                    for (int off = 8; off > 0; off >>= 1)
+                        tot += __shfl_xor_sync(0xffffffffu, tot, off);
+                    rowv[(2 * h) % RG] = __shfl_sync(0xffffffffu, tot, 0);
+                    if constexpr (RG >= 2)
+                        rowv[2 * h + 1] = __shfl_sync(0xffffffffu, tot, 16);
+                }
                 if (lane < C) {
-                    const unsigned int la = smem_u32(&xch[(g % kClXB) * 16 + rank]);
+                    const unsigned int la = smem_u32(&xch[(g % kClXB) * (RG * 8) + rank]);
                     const unsigned int lb = smem_u32(&xbar[g % kClXB]);
-                    st_remote(map_to_rank(la, (unsigned int)lane), tot);
-                    if constexpr (RG == 2)
-                        st_remote(map_to_rank(la + 8u * (unsigned int)sizeof(Acc), (unsigned int)lane), t1);
+#pragma unroll
+                    for (int r = 0; r < RG; ++r)
+                        st_remote(map_to_rank(la + (unsigned int)(r * 8 * sizeof(Acc)), (unsigned int)lane), rowv[r]);
                     arrive_remote(map_to_rank(lb, (unsigned int)lane));
                 }
             }
@@ -966,7 +975,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
                     break;
                 Acc dot = Acc(0);
                 for (int q = 0; q < C; ++q)
-                    dot += xch[(t % kClXB) * 16 + rr * 8 + q];
+                    dot += xch[(t % kClXB) * (RG * 8) + rr * 8 + q];
                 const unsigned char *row = stages + (size_t)(r % p.nstage) * p.stage_stride;
                 const Meta md = *reinterpret_cast<const Meta *>(row + meta_off);
                 const Acc sc = (Acc)meta_scale(md);
@@ -1038,9 +1047,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) map_cluster_kernel(const M
 // instances up to the register-resident limit of the storage type (8, 8,
 // 4, 2 vectors per thread for binary64, binary32, bf16, fp8)
 template <int S> constexpr int cluster_vpt_max() { return S == NSLI_BF16 ? 4 : (S == NSLI_FP8E4M3 ? 2 : 8); }
-// two rows per group for the storage types with short row slices (bf16,
-// FP8); binary64 and binary32 take one
-template <int S> constexpr int cluster_rg_max() { return (S == NSLI_BF16 || S == NSLI_FP8E4M3) ? 2 : 1; }
+// rows per group: up to four for FP8 and two for bf16 (short row slices,
+// whose fixed cost per group would otherwise dominate); binary64 and
+// binary32 take one
+template <int S> constexpr int cluster_rg_max() { return S == NSLI_FP8E4M3 ? 4 : (S == NSLI_BF16 ? 2 : 1); }
 template <int S, int RG> const void *cluster_fn_v(int vpt)
 {
     if (vpt == 1)
@@ -1061,6 +1071,10 @@ template <int S> const void *cluster_fn_s(int vpt, int rg)
 {
     if (rg == 1)
         return cluster_fn_v<S, 1>(vpt);
+    if constexpr (cluster_rg_max<S>() >= 4) {
+        if (rg == 4)
+            return cluster_fn_v<S, 4>(vpt);
+    }
     if constexpr (cluster_rg_max<S>() >= 2) {
         if (rg == 2)
             return cluster_fn_v<S, 2>(vpt);

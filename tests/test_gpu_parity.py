@@ -459,24 +459,27 @@ def test_long_rows_cluster_kernel_every_storage_and_size(monkeypatch, storage, m
 
 
 @pytest.mark.parametrize("storage,m,n,lag", [("bf16", 300, 40000, "1"), ("fp8", 200, 70000, "1"),
-                                            ("bf16", 37, 54000, "2")])
+                                            ("bf16", 37, 54000, "2"), ("fp8", 150, 54000, "1"),
+                                            ("fp8", 43, 54000, "2")])
 def test_long_rows_cluster_one_and_two_rows_per_group_agree(monkeypatch, storage, m, n, lag):
-    """bf16 and FP8 rows take two rows per block barrier on clusters (the
-    last group of a cluster's block may hold one); one row per barrier
-    (NSLI_LONG_CLUSTER_RG=1) does the same arithmetic in the same order, so
-    both give the same bits, and the one-row form keeps the parity bar."""
+    """bf16 rows take two rows per block barrier on clusters and FP8 rows
+    four (the last group of a cluster's block may hold fewer); one row per
+    barrier (NSLI_LONG_CLUSTER_RG=1) does the same arithmetic in the same
+    order, so every group size gives the same bits, and the one-row form
+    keeps the parity bar."""
     p = workloads.dense_system(m, n, seed=4100 + n)
     monkeypatch.setenv("NSLI_LONG_CLUSTER_LAG", lag)
     out = []
-    for rg in ("2", "1"):
+    for rg in (["4", "2", "1"] if storage == "fp8" else ["2", "1"]):
         monkeypatch.setenv("NSLI_LONG_CLUSTER_RG", rg)
         with nsli.Solver(p["A"], p["b0"], p["x0"], Av=p["Av"], storage=storage) as s:
             y, h, st = s.map_reduce()
             s.iterate(4, rho=1e-3)
             out.append((y, h, st, s.get_x()))
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
-    np.testing.assert_array_equal(out[0][3], out[1][3])
+    for o in out[1:]:
+        np.testing.assert_array_equal(out[0][0], o[0])
+        assert out[0][1] == o[1] and out[0][2] == o[2]
+        np.testing.assert_array_equal(out[0][3], o[3])
     test_long_rows_one_step_and_trajectory(storage, m, n)
 
 
